@@ -1,0 +1,47 @@
+"""Seeded input generators: determinism and the structure the configurations state."""
+import numpy as np
+
+import inputs
+
+
+def test_rmat_transition_structure():
+    a = inputs.rmat_transition(12, 16, 1).check()
+    b = inputs.rmat_transition(12, 16, 1)
+    assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)
+    assert np.array_equal(a.val, b.val)
+    rows = np.repeat(np.arange(a.n_rows), np.diff(a.row_ptr))
+    assert not np.any(rows == a.col)                       # self loops dropped
+    key = rows.astype(np.int64) * a.n_cols + a.col
+    assert np.all(np.diff(key) > 0)                        # sorted, no duplicates
+    colsum = np.bincount(a.col, weights=a.val, minlength=a.n_cols)
+    present = np.bincount(a.col, minlength=a.n_cols) > 0
+    assert np.allclose(colsum[present], 1.0, rtol=0, atol=1e-12)   # column stochastic
+    assert (~present).any()                                # dangling vertices kept
+    assert 0.8 * 16 * 4096 < a.nnz < 16 * 4096
+
+
+def test_rmat_seed_changes_graph():
+    a = inputs.rmat_transition(10, 8, 1)
+    b = inputs.rmat_transition(10, 8, 2)
+    assert a.nnz != b.nnz or not np.array_equal(a.col, b.col)
+
+
+def test_stress_variants():
+    base = inputs.rmat_uniform(12, 16, 3, 3).check()
+    assert np.all((base.val > 0) & (base.val <= 1))
+    e = inputs.empty_rows(base, 0.3, 4).check()
+    frac = (np.diff(e.row_ptr) == 0).mean() - (np.diff(base.row_ptr) == 0).mean()
+    assert 0.2 < frac < 0.35
+    h = inputs.add_hubs(base, 4, 1000, 3000, 5).check()
+    lens = np.diff(h.row_ptr)
+    assert sorted(lens[h.meta["hub_rows"]].tolist()) == sorted(h.meta["hub_lens"])
+    assert min(h.meta["hub_lens"]) > 700
+    er = inputs.erdos_renyi(1 << 12, 16, 6).check()
+    assert 15 * 4096 < er.nnz <= 16 * 4096
+
+
+def test_vectors():
+    x = inputs.uniform_vector(1000, 2)
+    assert np.all((x >= 0) & (x < 1)) and np.array_equal(x, inputs.uniform_vector(1000, 2))
+    u = inputs.uniform_open0(1000, 2)
+    assert np.all((u > 0) & (u <= 1))
