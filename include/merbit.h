@@ -1,0 +1,213 @@
+/*
+ * merbit.h — C ABI of a GB300 (sm_103a) implementation of MERBIT, the
+ * merge-path + bit-field-descriptor SpMV of Zhang, Yao, Jiang and Zhang,
+ * "MERBIT: A GPU-Based SpMV Method for Iterative Workloads", and of the
+ * PageRank power iteration built on it.
+ *
+ * Conventions for every call
+ *   - A CSR matrix is row_ptr (int32, n_rows + 1 entries, row_ptr[0] = 0,
+ *     row_ptr[n_rows] = nnz, non-decreasing) and col_idx (int32, nnz entries,
+ *     0 <= col < n_cols) as in Sec. 3.1; the row pointer is the paper's
+ *     `offset`, read as n_rows + 1 entries.  Columns need not be sorted.
+ *   - Unless a parameter says "host", every pointer is a DEVICE pointer of the
+ *     current CUDA device, owned by the caller.  `stream` is a cudaStream_t
+ *     (NULL = legacy default stream); calls are asynchronous on it unless
+ *     stated otherwise.
+ *   - `vals` and `col_idx` must be 16-byte aligned (they are staged into
+ *     shared memory by bulk copies); x / y / pi must be aligned to their
+ *     element size.
+ *   - Every call returns a merbit_status; on failure merbit_last_error()
+ *     returns a message (per calling thread).  Errors raised inside a kernel
+ *     (an expired bounded wait) are reported by the next synchronising call
+ *     (merbit_plan_sync, merbit_spmv_host, merbit_pagerank*) as
+ *     MERBIT_EDEVICE; that call also clears the plan's device state.
+ *   - A plan may be used by one stream at a time: its boundary-row
+ *     accumulators and reduction slots are shared by all its calls.
+ */
+#ifndef MERBIT_H
+#define MERBIT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct merbit_plan_s* merbit_plan_t;
+
+typedef enum merbit_status {
+  MERBIT_OK = 0,
+  MERBIT_EINVAL = 1,     /* invalid argument (message says which)                  */
+  MERBIT_EOVERFLOW = 2,  /* n_rows + nnz >= 2^31: merge-path coordinates are int32 */
+  MERBIT_ENOMEM = 3,     /* device allocation failed                               */
+  MERBIT_ECUDA = 4,      /* a CUDA runtime call failed                             */
+  MERBIT_ENOTCONV = 5,   /* PageRank hit max_iter before tol (result still written) */
+  MERBIT_EDEVICE = 6     /* a kernel reported an internal error (bounded wait)     */
+} merbit_status;
+
+typedef enum merbit_dtype {
+  MERBIT_F32 = 0,
+  MERBIT_F64 = 1,
+  MERBIT_BF16 = 2,
+  MERBIT_F16 = 3
+} merbit_dtype;
+
+typedef enum merbit_precision {
+  MERBIT_PLAIN = 0,    /* power iteration in the dtype of vals / pi                 */
+  MERBIT_IR_BF16 = 1,  /* iterative refinement, inner sweeps with bf16 values      */
+  MERBIT_IR_F16 = 2,   /* iterative refinement, inner sweeps with scaled f16 values */
+  MERBIT_IR_F32 = 3    /* iterative refinement, inner sweeps with f32 values       */
+} merbit_precision;
+
+/* Read-only view of a plan (the TILE arrays of Sec. 4.1.1 plus block data). */
+typedef struct merbit_plan_info {
+  int64_t n_rows, n_cols, nnz;
+  int32_t sigma;            /* steps per lane                                   */
+  int32_t omega;            /* lanes per tile (32, the warp size)               */
+  int32_t tiles_per_block;  /* tiles sharing one output buffer (W)              */
+  int64_t tile_num;         /* ceil((nnz + n_rows) / (omega * sigma))            */
+  int64_t lane_num;         /* ceil((nnz + n_rows) / sigma)                      */
+  int64_t block_num;        /* ceil(tile_num / tiles_per_block)                  */
+  const uint32_t* tile_x;   /* device, tile_num + 1: tile start x; last = nnz    */
+  const uint32_t* tile_y;   /* device, tile_num + 1: tile start row, MSB = single-row
+                               tile; last = n_rows                               */
+  const uint32_t* lane_desc;/* device, lane_num: bit_flag<<18 | y_off<<9 | x_off */
+  const int32_t* block_row; /* device, block_num + 1: row of each block's first
+                               coordinate (ROW(tile_y[b * W])); last = n_rows    */
+} merbit_plan_info;
+
+/*
+ * merbit_plan — build the reusable TILE schedule of a square n x n CSR matrix
+ * (Sec. 4.1, Algorithm generate_tile): merge-path search of every lane start
+ * on diagonal j*sigma, sigma-step walk into bit_flag, 32-bit lane descriptors
+ * and the single-row (MSB) tile mark.  sigma = 14, omega = 32, 8 tiles per
+ * block.  row_ptr is read during the call only; col_idx is BORROWED and must
+ * stay alive and unchanged until merbit_plan_destroy.  The plan owns all of
+ * its device memory.  Synchronises `stream` once (to read row_ptr[0] and
+ * row_ptr[n]).  Errors: EINVAL (NULL pointer, negative size, row_ptr[0] != 0
+ * or row_ptr[n] != nnz), EOVERFLOW, ENOMEM, ECUDA.
+ */
+merbit_status merbit_plan(const int32_t* row_ptr, const int32_t* col_idx, int64_t n,
+                          int64_t nnz, merbit_plan_t* out);
+
+/* As merbit_plan for an n_rows x n_cols matrix, with sigma in [1, 14]
+ * (32-bit descriptors need 2*ceil(log2(32*sigma)) + sigma <= 32, Sec. 4.1.1),
+ * tiles_per_block = 8, on `stream`. */
+merbit_status merbit_plan_ex(const int32_t* row_ptr, const int32_t* col_idx, int64_t n_rows,
+                             int64_t n_cols, int64_t nnz, int sigma, int tiles_per_block,
+                             void* stream, merbit_plan_t* out);
+
+/* Free a plan and everything it owns.  NULL is ignored.  Synchronises the device. */
+void merbit_plan_destroy(merbit_plan_t plan);
+
+/* Fill *info (host struct) with the plan's sizes and device array pointers
+ * (borrowed, valid until destroy).  Errors: EINVAL. */
+merbit_status merbit_plan_get_info(merbit_plan_t plan, merbit_plan_info* info);
+
+/* Copy the TILE arrays and block rows to HOST buffers (sizes as in
+ * merbit_plan_info: tile_num + 1, tile_num + 1, lane_num, block_num + 1);
+ * any pointer may be NULL to skip that array.  Synchronous (device-wide).
+ * Errors: EINVAL, ECUDA. */
+merbit_status merbit_plan_export(merbit_plan_t plan, uint32_t* tile_x, uint32_t* tile_y,
+                                 uint32_t* lane_desc, int32_t* block_row);
+
+/* Synchronise `stream` and report a kernel-side error of this plan's earlier
+ * asynchronous calls (EDEVICE; the plan's device state is reset). */
+merbit_status merbit_plan_sync(merbit_plan_t plan, void* stream);
+
+/*
+ * merbit_spmv — y = A x (Sec. 3.1) with the MERBIT kernel (Sec. 4.2,
+ * Algorithms MERBIT SpMV, tile_normal_tackle, WarpSegmentedSum): tile values
+ * and column indices staged in shared memory, descriptor-driven lane scan,
+ * warp segmented sum, single-row fast path, block commit.  dtype is F32 or F64
+ * for vals, x and y alike.  y (n_rows entries) is fully overwritten; the
+ * caller never clears it.  x has n_cols entries.  Asynchronous on the legacy
+ * default stream.  Errors: EINVAL (NULL, dtype, alignment), ECUDA.
+ */
+merbit_status merbit_spmv(merbit_plan_t plan, merbit_dtype dtype, const void* vals,
+                          const void* x, void* y);
+
+/*
+ * merbit_spmv_ex — as merbit_spmv with separate value / vector types and a
+ * stream.  Supported (vals_dtype, xy_dtype): (F32, F32), (F64, F64),
+ * (BF16, F32), (F16, F32); reduced-precision values are widened to f32 and
+ * accumulated in f32.  The result is multiplied by 2^-scale_exp (exact), for
+ * values stored pre-scaled by 2^scale_exp (see merbit_vals_convert); pass 0
+ * otherwise.
+ */
+merbit_status merbit_spmv_ex(merbit_plan_t plan, merbit_dtype vals_dtype, merbit_dtype xy_dtype,
+                             const void* vals, const void* x, void* y, int scale_exp,
+                             void* stream);
+
+/*
+ * merbit_spmv_host — y = A x with x and y in HOST memory (pinned or pageable;
+ * `vals` stays a device pointer).  x is copied into plan-owned device memory,
+ * the product runs on `stream`, y is copied back, and the stream is
+ * synchronised before returning.  dtype F32 or F64.  Errors as merbit_spmv,
+ * plus ENOMEM and EDEVICE.
+ */
+merbit_status merbit_spmv_host(merbit_plan_t plan, merbit_dtype dtype, const void* vals,
+                               const void* x_host, void* y_host, void* stream);
+
+/*
+ * merbit_vals_convert — round nnz values (src_dtype F64 or F32) to dst_dtype
+ * (BF16, F16 or F32), round-to-nearest-even.  With auto_scale != 0 and dst F16
+ * the values are first multiplied by 2^k, k the largest power keeping
+ * max|v| * 2^k below 2^15, so that small values of a stochastic matrix stay
+ * normal; k is written to *scale_exp_out (host, may be NULL) and must be passed
+ * as scale_exp to merbit_spmv_ex.  Synchronises `stream` when auto-scaling.
+ */
+merbit_status merbit_vals_convert(const void* src, merbit_dtype src_dtype, void* dst,
+                                  merbit_dtype dst_dtype, int64_t nnz, int auto_scale,
+                                  int* scale_exp_out, void* stream);
+
+/*
+ * merbit_pagerank — PageRank by the power method (Sec. 5.5.1) on a square
+ * plan whose values form P^T (column j holds 1/outdeg(j) for every edge j->i):
+ *   pi_0 = 1/n,  pi_{k+1} = alpha P^T pi_k + (alpha D_k + 1 - alpha)/n,
+ * D_k the mass of pi_k on dangling vertices (empty columns).  Stops once
+ * ||pi_{k+1} - pi_k||_1 < tol; at most 10000 updates.  dtype F32 or F64 (vals
+ * and pi).  pi (n entries) receives the last iterate.  One fused kernel per
+ * update (SpMV + update + residual + dangling mass, FP64 reductions).
+ * Synchronises the legacy default stream.  Errors: EINVAL (non-square plan,
+ * alpha outside [0,1), dtype), ENOTCONV, EDEVICE, ECUDA.
+ */
+merbit_status merbit_pagerank(merbit_plan_t plan, merbit_dtype dtype, const void* vals,
+                              double alpha, double tol, void* pi);
+
+/*
+ * merbit_pagerank_ex — as merbit_pagerank with:
+ *   max_iter     PLAIN: cap on updates.  IR modes: cap on refinement steps.
+ *                With tol <= 0 exactly max_iter updates (steps) run and the
+ *                call returns MERBIT_OK.
+ *   mode         PLAIN, or IR_BF16 / IR_F16 / IR_F32: mixed-precision
+ *                iterative refinement.  vals must be F64 (master values) and
+ *                pi F64.  Each step computes r = b - M pi in FP64
+ *                (M = I - alpha P^T - (alpha/n) 1 d^T, b = (1-alpha)/n 1), stops
+ *                when ||r||_1 < tol, then solves M delta = r approximately by
+ *                1 + inner_sweeps Richardson sweeps with reduced-precision
+ *                values, f32 vectors, f32 accumulation and FP64 dangling sums,
+ *                and sets pi += delta (FP64).
+ *   inner_sweeps IR modes: SpMV sweeps per refinement step (>= 1).
+ *   iters_out    host, may be NULL: updates (PLAIN) or refinement steps (IR).
+ *   resid_out    host, may be NULL: the last L1 residual computed.
+ *   resid_hist   host, may be NULL, max_iter entries: residual per update /
+ *                per refinement step.
+ * Synchronises `stream`.
+ */
+merbit_status merbit_pagerank_ex(merbit_plan_t plan, merbit_dtype dtype, const void* vals,
+                                 double alpha, double tol, int max_iter, merbit_precision mode,
+                                 int inner_sweeps, void* pi, int* iters_out, double* resid_out,
+                                 double* resid_hist, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* merbit_last_error(void);
+
+/* Library version string. */
+const char* merbit_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MERBIT_H */

@@ -1,0 +1,148 @@
+// Internal declarations of the MERBIT CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "merbit.h"
+
+namespace merbit {
+
+constexpr int kOmega = 32;          // lanes per tile = warp size (Sec. 4.3)
+constexpr int kSigmaMax = 14;       // largest sigma of the 32-bit descriptor (Sec. 4.1.1)
+constexpr int kTilesPerBlock = 8;   // W: tiles that share one shared-memory output buffer
+constexpr int kThreads = kTilesPerBlock * kOmega;   // one warp per tile
+constexpr int kRedSlots = 64;       // spread slots of the grid-wide FP64 reductions
+constexpr uint32_t kMsb = 0x80000000u;
+constexpr uint32_t kSpinLimit = 1u << 22;           // bounded mbarrier waits
+
+// Per-plan device state for grid-wide reductions and kernel-side errors.
+struct RedState {
+  double slot[kRedSlots][2];
+  unsigned int arrive;
+  int err;        // bit 0: an mbarrier wait expired
+  int done;       // PageRank: a fused launch found its residual below tol
+  int iters;      // number of launches counted when `done` was set
+};
+
+struct Geometry {
+  const uint32_t* tile_x;
+  const uint32_t* tile_y;
+  const uint32_t* lane_desc;
+  const int32_t* col;
+  const int32_t* bnd_row;
+  const int32_t* bnd_slot;
+  const int32_t* bnd_expect;
+  double* bnd_acc;
+  unsigned int* bnd_cnt;
+  RedState* red;
+  int n_rows;
+  int nnz;
+  int steps;       // nnz + n_rows
+  int sigma;
+  int tile_num;
+  int lane_num;
+  int nb;          // number of blocks of tiles
+};
+
+}  // namespace merbit
+
+struct merbit_plan_s {
+  int device = 0;
+  int num_sms = 0;
+  int64_t n_rows = 0, n_cols = 0, nnz = 0;
+  int sigma = 14, tiles_per_block = merbit::kTilesPerBlock;
+  int64_t tile_num = 0, lane_num = 0, nb = 0;
+  const int32_t* col = nullptr;          // borrowed
+  uint32_t* tile_x = nullptr;
+  uint32_t* tile_y = nullptr;
+  uint32_t* lane_desc = nullptr;
+  int32_t* bnd_row = nullptr;
+  int32_t* bnd_slot = nullptr;
+  int32_t* bnd_expect = nullptr;
+  double* bnd_acc = nullptr;
+  unsigned int* bnd_cnt = nullptr;
+  merbit::RedState* red = nullptr;
+  // lazily built PageRank data
+  uint32_t* dangling_bits = nullptr;     // (n+31)/32 words, bit set = dangling vertex
+  int64_t n_dangling = -1;
+  // scratch owned by the plan (grown on demand)
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  double* hist = nullptr;                // per-launch reduction results, [launch][2]
+  size_t hist_len = 0;
+  void* x_stage = nullptr;               // staging for host-buffer SpMV
+  void* y_stage = nullptr;
+  size_t x_stage_bytes = 0, y_stage_bytes = 0;
+  void* host_pinned = nullptr;           // small pinned block for state read-back
+
+  merbit::Geometry geom() const {
+    merbit::Geometry g;
+    g.tile_x = tile_x; g.tile_y = tile_y; g.lane_desc = lane_desc; g.col = col;
+    g.bnd_row = bnd_row; g.bnd_slot = bnd_slot; g.bnd_expect = bnd_expect;
+    g.bnd_acc = bnd_acc; g.bnd_cnt = bnd_cnt; g.red = red;
+    g.n_rows = (int)n_rows; g.nnz = (int)nnz; g.steps = (int)(nnz + n_rows);
+    g.sigma = sigma; g.tile_num = (int)tile_num; g.lane_num = (int)lane_num; g.nb = (int)nb;
+    return g;
+  }
+};
+
+namespace merbit {
+
+// ---- epilogue parameter blocks (device-side behaviour lives in spmv_kernel.cuh) ----
+
+// PageRank power update: out = alpha*s + (alpha*D + 1 - alpha)/n.
+struct PRParams {
+  void* out;                    // T[n]: pi_{k+1}
+  const uint32_t* dang;         // dangling bits
+  double alpha, inv_n, tol;
+  const double* d_in;           // D_k (dangling mass of pi_k)
+  double* s_out;                // [0] = ||pi_{k+1} - pi_k||_1, [1] = D_{k+1}
+  int iter;                     // launch index, stored in red->iters on convergence
+};
+
+// Mixed-precision refinement: residual r = b - M pi in FP64.
+struct ResidParams {
+  float* rhs;                   // f32 copy of r (= first inner iterate)
+  const uint32_t* dang;
+  double alpha, inv_n, tol;
+  const double* d_in;           // D of pi
+  double* s_out;                // [0] = ||r||_1, [1] = dangling sum of rhs
+  int iter;
+};
+
+// Mixed-precision refinement: one inner Richardson sweep.
+struct SweepParams {
+  float* out;                   // next inner iterate (unused when last)
+  const float* rhs;
+  const uint32_t* dang;
+  double alpha, inv_n;
+  float scale;                  // 2^-scale_exp of pre-scaled values
+  const double* d_in;           // dangling sum of the current inner iterate
+  double* s_out;                // [0] = L1 step size, [1] = dangling sum (of pi when last)
+  double* pi64;                 // updated in place when last
+  int last;
+};
+
+// ---- launchers (one translation unit per value type) ----
+cudaError_t spmv_plain_f32(const merbit_plan_s* p, const float* vals, const float* x, float* y,
+                           cudaStream_t st);
+cudaError_t spmv_plain_f64(const merbit_plan_s* p, const double* vals, const double* x,
+                           double* y, cudaStream_t st);
+cudaError_t spmv_plain_lo(const merbit_plan_s* p, merbit_dtype vdt, const void* vals,
+                          const float* x, float* y, float scale, cudaStream_t st);
+cudaError_t spmv_pr_f32(const merbit_plan_s* p, const float* vals, const float* x,
+                        const PRParams& prm, cudaStream_t st);
+cudaError_t spmv_pr_f64(const merbit_plan_s* p, const double* vals, const double* x,
+                        const PRParams& prm, cudaStream_t st);
+cudaError_t spmv_resid_f64(const merbit_plan_s* p, const double* vals, const double* pi,
+                           const ResidParams& prm, cudaStream_t st);
+cudaError_t spmv_sweep(const merbit_plan_s* p, merbit_dtype vdt, const void* vals,
+                       const float* x, const SweepParams& prm, cudaStream_t st);
+
+// Largest grid worth launching for a kernel (SMs x resident CTAs), cached.
+int persistent_grid(const void* kernel, int threads, size_t smem, int num_sms);
+
+}  // namespace merbit

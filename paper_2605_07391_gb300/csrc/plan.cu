@@ -1,0 +1,202 @@
+// Plan construction (Sec. 4.1.2, Algorithm generate_tile) and the block
+// boundary data used by the SpMV commit.
+#include <mutex>
+#include <map>
+
+#include "merbit_internal.cuh"
+
+namespace merbit {
+
+// Number of down steps among the first d steps of the merge path, i.e. the row
+// of the path coordinate on diagonal d (Sec. 3.3, Algorithm merge_search).
+// Row y's down step is step row_ptr[y+1] + y, so the answer is the smallest y
+// with row_ptr[y+1] + y >= d (or n_rows).  The search is confined to
+// [max(d - nnz, 0), min(d, n_rows)] because x = d - y lies in [0, nnz].
+__device__ __forceinline__ int rows_before(const int32_t* __restrict__ row_ptr, int n_rows,
+                                           int nnz, int d) {
+  int lo = max(d - nnz, 0);
+  int hi = min(d, n_rows);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(row_ptr + mid + 1) + mid < d)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// One thread per lane j: start coordinate on diagonal j*sigma, sigma-step walk
+// into bit_flag, descriptor packing; lane 0 of each warp (= tile) writes the
+// tile start, with the MSB set when no lane of the tile takes a down step.
+__global__ void plan_tiles_kernel(const int32_t* __restrict__ row_ptr, int n_rows, int nnz,
+                                  int sigma, int lane_num, int tile_num,
+                                  uint32_t* __restrict__ tile_x, uint32_t* __restrict__ tile_y,
+                                  uint32_t* __restrict__ lane_desc) {
+  const int64_t j64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool active = j64 < lane_num;
+  const int j = (int)(j64 < (int64_t)lane_num ? j64 : (int64_t)lane_num);
+  const int steps = nnz + n_rows;
+  int cx = 0, cy = 0;
+  if (active) {
+    const int d = j * sigma;
+    cy = rows_before(row_ptr, n_rows, nnz, d);
+    cx = d - cy;
+  }
+  const int tx = __shfl_sync(0xffffffffu, cx, 0);
+  const int ty = __shfl_sync(0xffffffffu, cy, 0);
+  int end_y = ty;
+  if (active) {
+    const int len = min(sigma, steps - j * sigma);
+    int x = cx, y = cy;
+    int row_end = y < n_rows ? __ldg(row_ptr + y + 1) : nnz;
+    uint32_t flags = 0;
+    for (int k = 0; k < len; ++k) {
+      if (x < row_end) {
+        ++x;                       // right step: next nonzero of row y
+      } else {
+        flags |= 1u << k;          // down step: row y is complete
+        ++y;
+        row_end = y < n_rows ? __ldg(row_ptr + y + 1) : nnz;
+      }
+    }
+    lane_desc[j] = (flags << 18) | ((uint32_t)(cy - ty) << 9) | (uint32_t)(cx - tx);
+    end_y = y;
+  }
+  const bool single_row = __all_sync(0xffffffffu, end_y == ty);
+  if (active && lane == 0) {
+    const int i = j / kOmega;
+    tile_x[i] = (uint32_t)tx;
+    tile_y[i] = (uint32_t)ty | (single_row ? kMsb : 0u);
+  }
+  if (j64 == lane_num) {
+    tile_x[tile_num] = (uint32_t)nnz;
+    tile_y[tile_num] = (uint32_t)n_rows;
+  }
+}
+
+// bnd_row[b] = ROW(tile_y[min(b*W, tile_num)]) for b = 0..nb.
+__global__ void plan_block_rows_kernel(const uint32_t* __restrict__ tile_y, int tile_num, int W,
+                                       int nb, int32_t* __restrict__ bnd_row) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > nb) return;
+  bnd_row[b] = (int32_t)(tile_y[min(b * W, tile_num)] & ~kMsb);
+}
+
+// bnd_slot[b] = first index b' with bnd_row[b'] == bnd_row[b] (bnd_row is sorted).
+__global__ void plan_slots_kernel(const int32_t* __restrict__ bnd_row, int nb,
+                                  int32_t* __restrict__ bnd_slot) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > nb) return;
+  const int key = bnd_row[b];
+  int lo = 0, hi = b;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (bnd_row[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  bnd_slot[b] = lo;
+}
+
+// Arrivals per boundary slot: block v contributes its first row, and its last
+// row when that row differs from the first and exists.
+__global__ void plan_expect_kernel(const int32_t* __restrict__ bnd_row,
+                                   const int32_t* __restrict__ bnd_slot, int nb, int n_rows,
+                                   int32_t* __restrict__ expect) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nb) return;
+  atomicAdd(expect + bnd_slot[v], 1);
+  if (bnd_row[v + 1] != bnd_row[v] && bnd_row[v + 1] < n_rows) atomicAdd(expect + bnd_slot[v + 1], 1);
+}
+
+__global__ void mark_columns_kernel(const int32_t* __restrict__ col, int nnz,
+                                    uint8_t* __restrict__ present) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x)
+    present[__ldg(col + k)] = 1;
+}
+
+__global__ void dangling_bits_kernel(const uint8_t* __restrict__ present, int n,
+                                     uint32_t* __restrict__ bits,
+                                     unsigned long long* __restrict__ count) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  const int words = (n + 31) >> 5;
+  if (w >= words) return;
+  uint32_t b = 0;
+  for (int i = 0; i < 32; ++i) {
+    const int r = w * 32 + i;
+    if (r < n && !present[r]) b |= 1u << i;
+  }
+  bits[w] = b;
+  if (b) atomicAdd(count, (unsigned long long)__popc(b));
+}
+
+cudaError_t build_tiles(const merbit_plan_s* p, const int32_t* row_ptr, cudaStream_t st) {
+  if (p->lane_num == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t total = p->lane_num + 1;
+  const int blocks = (int)((total + threads - 1) / threads);
+  plan_tiles_kernel<<<blocks, threads, 0, st>>>(row_ptr, (int)p->n_rows, (int)p->nnz, p->sigma,
+                                                (int)p->lane_num, (int)p->tile_num, p->tile_x,
+                                                p->tile_y, p->lane_desc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nbt = (int)((p->nb + 1 + threads - 1) / threads);
+  plan_block_rows_kernel<<<nbt, threads, 0, st>>>(p->tile_y, (int)p->tile_num, p->tiles_per_block,
+                                                  (int)p->nb, p->bnd_row);
+  plan_slots_kernel<<<nbt, threads, 0, st>>>(p->bnd_row, (int)p->nb, p->bnd_slot);
+  e = cudaMemsetAsync(p->bnd_expect, 0, sizeof(int32_t) * (p->nb + 1), st);
+  if (e != cudaSuccess) return e;
+  plan_expect_kernel<<<nbt, threads, 0, st>>>(p->bnd_row, p->bnd_slot, (int)p->nb, (int)p->n_rows,
+                                              p->bnd_expect);
+  return cudaGetLastError();
+}
+
+cudaError_t build_dangling(merbit_plan_s* p, cudaStream_t st, unsigned long long* host_count) {
+  const int n = (int)p->n_cols;
+  uint8_t* present = nullptr;
+  unsigned long long* cnt = nullptr;
+  cudaError_t e = cudaMalloc(&present, (size_t)n + 8);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&cnt, sizeof(unsigned long long));
+  if (e != cudaSuccess) { cudaFree(present); return e; }
+  const size_t words = ((size_t)n + 31) / 32;
+  if (!p->dangling_bits) {
+    e = cudaMalloc(&p->dangling_bits, words * sizeof(uint32_t) + 4);
+    if (e != cudaSuccess) { cudaFree(present); cudaFree(cnt); return e; }
+  }
+  cudaMemsetAsync(present, 0, (size_t)n, st);
+  cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+  if (p->nnz > 0) {
+    const int blocks = p->num_sms * 8;
+    mark_columns_kernel<<<blocks, 256, 0, st>>>(p->col, (int)p->nnz, present);
+  }
+  dangling_bits_kernel<<<(int)((words + 255) / 256), 256, 0, st>>>(present, n, p->dangling_bits, cnt);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_count, cnt, sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(present);
+  cudaFree(cnt);
+  return e;
+}
+
+int persistent_grid(const void* kernel, int threads, size_t smem, int num_sms) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(kernel, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second * num_sms;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
+    return 0;
+  cache[key] = per_sm;
+  return per_sm * num_sms;
+}
+
+}  // namespace merbit

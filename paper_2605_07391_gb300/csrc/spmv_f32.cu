@@ -1,0 +1,20 @@
+// f32 values, f32 vectors: plain SpMV and the fused PageRank update.
+#include "spmv_kernel.cuh"
+
+namespace merbit {
+
+cudaError_t spmv_plain_f32(const merbit_plan_s* p, const float* vals, const float* x, float* y,
+                           cudaStream_t st) {
+  EpiPlain<float, float> epi{y, 1.0f};
+  return launch_spmv<float, float, float>(p, vals, x, epi, st);
+}
+
+cudaError_t spmv_pr_f32(const merbit_plan_s* p, const float* vals, const float* x,
+                        const PRParams& prm, cudaStream_t st) {
+  EpiPageRank<float> epi{};
+  epi.p = prm;
+  epi.xold = x;
+  return launch_spmv<float, float, float>(p, vals, x, epi, st);
+}
+
+}  // namespace merbit

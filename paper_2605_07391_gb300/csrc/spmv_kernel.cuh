@@ -1,0 +1,560 @@
+// MERBIT SpMV kernel for sm_103a (Sec. 4.2: Algorithms MERBIT SpMV,
+// tile_normal_tackle, WarpSegmentedSum) with a pluggable row epilogue.
+//
+// Work unit: a block of W = 8 consecutive tiles (omega*sigma merge-path steps
+// each), one warp per tile, exactly as in the paper.  GB300-specific choices:
+//   * persistent CTAs (grid = SMs x resident CTAs) walk the blocks with a
+//     stride, with two shared-memory stages: while block v is reduced, the
+//     values and column indices of the CTA's next block are already in flight
+//     as two cp.async.bulk copies completing on an mbarrier (the block's
+//     nonzero range is contiguous, so one bulk copy per array suffices);
+//   * matrix streams use an L2 evict_first policy, the x gather an
+//     evict_last policy (x is reused by every block and, in PageRank, by the
+//     next launch);
+//   * products overwrite the staged values (or column indices for 16-bit
+//     values) in place and the block's row partial sums follow them, so one
+//     stage holds W*omega*sigma + 16 elements of each array (Sec. 4.3's
+//     (b+1)*sigma bound, re-derived for this layout);
+//   * rows shared between blocks (the block's first and last row) are added
+//     into per-row FP64 accumulators; the last CTA to arrive at a row (counted
+//     against the arrival count fixed by the plan) finalises it and clears
+//     the accumulator, so outputs are written exactly once and no vector
+//     ever needs clearing between calls (the role of the paper's dual-buffer
+//     commit, which resets only block-boundary rows).
+#pragma once
+
+#include "merbit_internal.cuh"
+
+namespace merbit {
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for an mbarrier phase with an iteration cap; false if the cap expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ float ld_x(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ double ld_x(const double* p, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float widen(__half v) { return __half2float(v); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ bool is_dangling(const uint32_t* bits, int r) {
+  return (__ldg(bits + (r >> 5)) >> (r & 31)) & 1u;
+}
+
+__device__ __forceinline__ double read_reset(double* p) {
+  return __longlong_as_double(
+      static_cast<long long>(atomicExch(reinterpret_cast<unsigned long long*>(p), 0ull)));
+}
+
+// ---------------------------------------------------------------- epilogues
+// row(r, s)   : complete sum s of interior row r (accumulator type)
+// row64(r, s) : complete FP64 sum of a block-boundary row
+// Each may add to the two FP64 reduction partials p0, p1.
+
+template <typename XT, typename AT>
+struct EpiPlain {
+  static constexpr bool kReduce = false;
+  XT* y;
+  AT scale;
+  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ bool skip(const RedState*) const { return false; }
+  __device__ __forceinline__ void row(int r, AT s, double&, double&) const {
+    y[r] = static_cast<XT>(s * scale);
+  }
+  __device__ __forceinline__ void row64(int r, double s, double&, double&) const {
+    y[r] = static_cast<XT>(s * static_cast<double>(scale));
+  }
+  __device__ __forceinline__ void finish(double, double, RedState*) const {}
+};
+
+// pi_{k+1}[r] = alpha * (P^T pi_k)[r] + (alpha D_k + 1 - alpha) / n   (Sec. 5.5.1)
+template <typename T>
+struct EpiPageRank {
+  static constexpr bool kReduce = true;
+  PRParams p;
+  const T* xold;
+  T a, c;
+  double cd;
+  __device__ __forceinline__ void init() {
+    const double D = *p.d_in;
+    cd = (p.alpha * D + 1.0 - p.alpha) * p.inv_n;
+    a = static_cast<T>(p.alpha);
+    c = static_cast<T>(cd);
+  }
+  __device__ __forceinline__ bool skip(const RedState* red) const {
+    return *reinterpret_cast<const volatile int*>(&red->done) != 0;
+  }
+  __device__ __forceinline__ void put(int r, T v, double& p0, double& p1) const {
+    static_cast<T*>(p.out)[r] = v;
+    p0 += fabs(static_cast<double>(v) - static_cast<double>(xold[r]));
+    if (is_dangling(p.dang, r)) p1 += static_cast<double>(v);
+  }
+  __device__ __forceinline__ void row(int r, T s, double& p0, double& p1) const {
+    put(r, a * s + c, p0, p1);
+  }
+  __device__ __forceinline__ void row64(int r, double s, double& p0, double& p1) const {
+    put(r, static_cast<T>(p.alpha * s + cd), p0, p1);
+  }
+  __device__ __forceinline__ void finish(double A, double B, RedState* red) const {
+    p.s_out[0] = A;
+    p.s_out[1] = B;
+    if (p.tol > 0.0 && A < p.tol) {
+      red->iters = p.iter + 1;
+      red->done = 1;
+    }
+  }
+};
+
+// r = (1-alpha)/n + alpha (P^T pi) + (alpha/n) D_pi - pi   (FP64)
+struct EpiResid {
+  static constexpr bool kReduce = true;
+  ResidParams p;
+  const double* pi;
+  double base;
+  __device__ __forceinline__ void init() {
+    base = (1.0 - p.alpha) * p.inv_n + p.alpha * p.inv_n * (*p.d_in);
+  }
+  __device__ __forceinline__ bool skip(const RedState* red) const {
+    return *reinterpret_cast<const volatile int*>(&red->done) != 0;
+  }
+  __device__ __forceinline__ void row64(int r, double s, double& p0, double& p1) const {
+    const double rr = base + p.alpha * s - pi[r];
+    const float rf = static_cast<float>(rr);
+    p.rhs[r] = rf;
+    p0 += fabs(rr);
+    if (is_dangling(p.dang, r)) p1 += static_cast<double>(rf);
+  }
+  __device__ __forceinline__ void row(int r, double s, double& p0, double& p1) const {
+    row64(r, s, p0, p1);
+  }
+  __device__ __forceinline__ void finish(double A, double B, RedState* red) const {
+    p.s_out[0] = A;
+    p.s_out[1] = B;
+    if (A < p.tol) {
+      red->iters = p.iter + 1;
+      red->done = 1;
+    }
+  }
+};
+
+// delta'[r] = alpha 2^-k (P~^T delta)[r] + (alpha/n) D_delta + rhs[r]; last sweep: pi += delta'
+struct EpiSweep {
+  static constexpr bool kReduce = true;
+  SweepParams p;
+  const float* xin;
+  float as, c;
+  __device__ __forceinline__ void init() {
+    as = static_cast<float>(p.alpha) * p.scale;
+    c = static_cast<float>(p.alpha * p.inv_n * (*p.d_in));
+  }
+  __device__ __forceinline__ bool skip(const RedState* red) const {
+    return *reinterpret_cast<const volatile int*>(&red->done) != 0;
+  }
+  __device__ __forceinline__ void put(int r, float d, double& p0, double& p1) const {
+    if (!p.last) {
+      p.out[r] = d;
+      p0 += fabs(static_cast<double>(d) - static_cast<double>(xin[r]));
+      if (is_dangling(p.dang, r)) p1 += static_cast<double>(d);
+    } else {
+      const double v = p.pi64[r] + static_cast<double>(d);
+      p.pi64[r] = v;
+      p0 += fabs(static_cast<double>(d));
+      if (is_dangling(p.dang, r)) p1 += v;
+    }
+  }
+  __device__ __forceinline__ void row(int r, float s, double& p0, double& p1) const {
+    put(r, as * s + (c + p.rhs[r]), p0, p1);
+  }
+  __device__ __forceinline__ void row64(int r, double s, double& p0, double& p1) const {
+    put(r, static_cast<float>(static_cast<double>(as) * s) + (c + p.rhs[r]), p0, p1);
+  }
+  __device__ __forceinline__ void finish(double A, double B, RedState*) const {
+    p.s_out[0] = A;
+    p.s_out[1] = B;
+  }
+};
+
+// ---------------------------------------------------------------- kernel
+
+struct StageInfo {
+  int x_bs, x_be, y_bs, y_be;   // block start / end coordinates
+  int a0v, endv;                // values staged for [a0v, endv)
+  int a0c, endc;                // column indices staged for [a0c, endc)
+};
+
+template <typename VT>
+__host__ __device__ constexpr int stage_cap(int sigma) {
+  return kThreads * sigma + 16;
+}
+
+__host__ __device__ inline size_t round128(size_t b) { return (b + 127) & ~size_t(127); }
+
+template <typename VT>
+__host__ __device__ inline size_t stage_vals_bytes(int sigma) {
+  return round128(sizeof(VT) * (size_t)stage_cap<VT>(sigma));
+}
+template <typename VT>
+__host__ __device__ inline size_t stage_col_bytes(int sigma) {
+  return round128(sizeof(int32_t) * (size_t)stage_cap<VT>(sigma));
+}
+template <typename VT>
+__host__ __device__ inline size_t stage_bytes(int sigma) {
+  return stage_vals_bytes<VT>(sigma) + stage_col_bytes<VT>(sigma);
+}
+
+// Products go where an input of the same width was staged.
+template <typename VT, typename AT>
+struct ProdInVals {
+  static constexpr bool value = sizeof(VT) == sizeof(AT);
+};
+
+template <typename VT, typename XT, typename AT, typename Epi>
+__global__ void __launch_bounds__(kThreads, 2)
+    merbit_spmv_kernel(const Geometry g, const VT* __restrict__ vals, const XT* __restrict__ x,
+                       Epi epi) {
+  static_assert(ProdInVals<VT, AT>::value || sizeof(AT) == 4, "product slot width");
+  constexpr int VE = 16 / (int)sizeof(VT);   // values per 16 bytes
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ StageInfo info[2];
+  __shared__ double red_smem[kThreads / 32][2];
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int G = gridDim.x;
+  if (epi.skip(g.red)) return;
+  epi.init();
+
+  const size_t svb = stage_vals_bytes<VT>(g.sigma);
+  const size_t stb = stage_bytes<VT>(g.sigma);
+  auto sv = [&](int s) { return reinterpret_cast<VT*>(dyn_smem + (size_t)s * stb); };
+  auto sc = [&](int s) { return reinterpret_cast<int32_t*>(dyn_smem + (size_t)s * stb + svb); };
+
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_x = policy_evict_last();
+  const int nnz_v = g.nnz & ~(VE - 1);
+  const int nnz_c = g.nnz & ~3;
+
+  // geometry of block v, as needed to issue its copies (thread 0 only)
+  auto geom_of = [&](int v, int& xb, int& xe, uint32_t& yb, uint32_t& ye) {
+    const int bs = v * kTilesPerBlock;
+    const int be = min(bs + kTilesPerBlock, g.tile_num);
+    xb = (int)g.tile_x[bs];
+    xe = (int)g.tile_x[be];
+    yb = g.tile_y[bs] & ~kMsb;
+    ye = g.tile_y[be] & ~kMsb;
+  };
+  auto issue = [&](int s, int xb, int xe, uint32_t yb, uint32_t ye) {
+    StageInfo in;
+    in.x_bs = xb; in.x_be = xe; in.y_bs = (int)yb; in.y_be = (int)ye;
+    in.a0v = xb & ~(VE - 1);
+    in.endv = max(in.a0v, min((xe + VE - 1) & ~(VE - 1), nnz_v));
+    in.a0c = xb & ~3;
+    in.endc = max(in.a0c, min((xe + 3) & ~3, nnz_c));
+    info[s] = in;
+    const uint32_t bv = (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT);
+    const uint32_t bc = (uint32_t)(in.endc - in.a0c) * 4u;
+    mbar_arrive_expect_tx(&mbar[s], bv + bc);
+    if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, &mbar[s], pol_stream);
+    if (bc) bulk_g2s(sc(s), g.col + in.a0c, bc, &mbar[s], pol_stream);
+  };
+
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int xb, xe; uint32_t yb, ye;
+    if (blockIdx.x < g.nb) { geom_of(blockIdx.x, xb, xe, yb, ye); issue(0, xb, xe, yb, ye); }
+    if (blockIdx.x + G < g.nb) { geom_of(blockIdx.x + G, xb, xe, yb, ye); issue(1, xb, xe, yb, ye); }
+  }
+
+  double p0 = 0.0, p1 = 0.0;
+  int it = 0;
+  for (int v = blockIdx.x; v < g.nb; v += G, ++it) {
+    const int s = it & 1;
+    const uint32_t par = (it >> 1) & 1;
+
+    // tile metadata of this warp, loaded before the wait to hide latency
+    const int ti = v * kTilesPerBlock + warp;
+    const bool tile_ok = ti < g.tile_num;
+    uint32_t txs = 0, txe = 0, tys = 0, desc = 0;
+    const int j = ti * kOmega + lane;
+    if (tile_ok) {
+      txs = __ldg(g.tile_x + ti);
+      txe = __ldg(g.tile_x + ti + 1);
+      tys = __ldg(g.tile_y + ti);
+      if (!(tys & kMsb) && j < g.lane_num) desc = __ldg(g.lane_desc + j);
+    }
+    // geometry for the copy issued at the end of this iteration
+    int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
+    const bool refill = (tid == 0) && (v + 2 * G < g.nb);
+    if (refill) geom_of(v + 2 * G, nxb, nxe, nyb, nye);
+
+    const bool ok = mbar_wait_bounded(&mbar[s], par);
+    if (__syncthreads_or(!ok)) {
+      // expired wait: record it, let this CTA's copies land (bounded), leave
+      if (tid == 0) atomicOr(&g.red->err, 1);
+      mbar_wait_bounded(&mbar[s], par);
+      if (v + G < g.nb) mbar_wait_bounded(&mbar[s ^ 1], ((it + 1) >> 1) & 1);
+      return;
+    }
+    const StageInfo in = info[s];
+    AT* prod;
+    int pb;
+    if constexpr (ProdInVals<VT, AT>::value) {
+      prod = reinterpret_cast<AT*>(sv(s));
+      pb = in.a0v;
+    } else {
+      prod = reinterpret_cast<AT*>(sc(s));
+      pb = in.a0c;
+    }
+
+    // ---- stage products val * x[col] (load_smem of Algorithm MERBIT SpMV)
+    {
+      const int cnt = in.x_be - in.x_bs;
+      int cidx[kSigmaMax];
+      AT vv[kSigmaMax];
+#pragma unroll
+      for (int u = 0; u < kSigmaMax; ++u) {
+        const int k = in.x_bs + tid + u * kThreads;
+        cidx[u] = 0;
+        vv[u] = AT(0);
+        if (tid + u * kThreads < cnt) {
+          cidx[u] = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
+          vv[u] = static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
+        }
+      }
+      AT xv[kSigmaMax];
+#pragma unroll
+      for (int u = 0; u < kSigmaMax; ++u)
+        xv[u] = (tid + u * kThreads < cnt) ? static_cast<AT>(ld_x(x + cidx[u], pol_x)) : AT(0);
+#pragma unroll
+      for (int u = 0; u < kSigmaMax; ++u) {
+        const int k = in.x_bs + tid + u * kThreads;
+        if (tid + u * kThreads < cnt) prod[k - pb] = vv[u] * xv[u];
+      }
+    }
+    AT* s_y = prod + (in.x_be - pb);
+    for (int r = tid; r <= in.y_be - in.y_bs; r += kThreads) s_y[r] = AT(0);
+    __syncthreads();
+
+    // ---- per-tile reduction (tile_fast_tackle / tile_normal_tackle + WarpSegmentedSum)
+    if (tile_ok && txs < txe) {
+      const int y_ws = (int)(tys & ~kMsb);
+      AT* sy = s_y + (y_ws - in.y_bs);
+      const AT* pt = prod + ((int)txs - pb);
+      if (tys & kMsb) {
+        // single-row tile: plain warp reduction, no descriptor
+        AT sum = AT(0);
+        for (int k = lane; k < (int)(txe - txs); k += 32) sum += pt[k];
+        sum = warp_sum(sum);
+        if (lane == 0) atomicAdd(sy, sum);
+      } else {
+        const bool active = j < g.lane_num;
+        const int lane_len = active ? min(g.sigma, g.steps - j * g.sigma) : 0;
+        int xo = (int)(desc & 511u);
+        int yo = active ? (int)((desc >> 9) & 511u) : (g.n_rows - y_ws);
+        const uint32_t fl = desc >> 18;
+        AT sum = AT(0);
+        bool first = true;
+        bool head = lane == 0;
+#pragma unroll
+        for (int k = 0; k < kSigmaMax; ++k) {
+          if (k < lane_len) {
+            if ((fl >> k) & 1u) {
+              // down step: the row in progress ends inside this lane
+              if (first) {
+                atomicAdd(sy + yo, sum);   // the row may have begun in earlier lanes
+                first = false;
+              } else {
+                sy[yo] = sum;              // the row lies entirely in this lane
+              }
+              sum = AT(0);
+              ++yo;
+              head = true;
+            } else {
+              sum += pt[xo];
+              ++xo;
+            }
+          }
+        }
+        // segmented inclusive scan of trailing sums; heads start segments
+        AT sv_ = sum;
+        int f = head ? 1 : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          if (__all_sync(0xffffffffu, f)) break;
+          const AT up = __shfl_up_sync(0xffffffffu, sv_, o);
+          const int fu = __shfl_up_sync(0xffffffffu, f, o);
+          if (lane >= o && !f) {
+            sv_ += up;
+            f = fu;
+          }
+        }
+        // a head lane adds the segment that ends just before it; lane 0 takes
+        // the tile's final segment (ending at lane 31)
+        const int src = lane == 0 ? 31 : lane - 1;
+        const AT seg = __shfl_sync(0xffffffffu, sv_, src);
+        const int row = __shfl_sync(0xffffffffu, yo, src);
+        if (head) atomicAdd(sy + row, seg);
+      }
+    }
+    __syncthreads();
+
+    // ---- block commit: interior rows complete here, boundary rows via FP64 accumulators
+    for (int r = in.y_bs + 1 + tid; r < in.y_be; r += kThreads) epi.row(r, s_y[r - in.y_bs], p0, p1);
+    if ((tid & 31) == 0 && tid < 64) {
+      const int which = tid >> 5;
+      const int r = which ? in.y_be : in.y_bs;
+      const bool contributes = which == 0 || (in.y_be != in.y_bs && in.y_be < g.n_rows);
+      if (contributes) {
+        const int slot = __ldg(g.bnd_slot + v + which);
+        atomicAdd(g.bnd_acc + slot, static_cast<double>(s_y[r - in.y_bs]));
+        __threadfence();
+        const unsigned int t = atomicAdd(g.bnd_cnt + slot, 1u);
+        if (t + 1 == (unsigned int)__ldg(g.bnd_expect + slot)) {
+          __threadfence();
+          const double tot = read_reset(g.bnd_acc + slot);
+          g.bnd_cnt[slot] = 0u;
+          epi.row64(r, tot, p0, p1);
+        }
+      }
+    }
+    // stage s is free again once every thread is past this point
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (refill) issue(s, nxb, nxe, nyb, nye);
+  }
+
+  if constexpr (Epi::kReduce) {
+    p0 = warp_sum(p0);
+    p1 = warp_sum(p1);
+    if (lane == 0) {
+      red_smem[warp][0] = p0;
+      red_smem[warp][1] = p1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) {
+        a += red_smem[w][0];
+        b += red_smem[w][1];
+      }
+      RedState* red = g.red;
+      const int q = blockIdx.x % kRedSlots;
+      atomicAdd(&red->slot[q][0], a);
+      atomicAdd(&red->slot[q][1], b);
+      __threadfence();
+      const unsigned int t = atomicAdd(&red->arrive, 1u);
+      if (t + 1 == gridDim.x) {
+        __threadfence();
+        double A = 0.0, B = 0.0;
+        for (int i = 0; i < kRedSlots; ++i) {
+          A += read_reset(&red->slot[i][0]);
+          B += read_reset(&red->slot[i][1]);
+        }
+        red->arrive = 0u;
+        epi.finish(A, B, red);
+      }
+    }
+  }
+}
+
+template <typename VT, typename XT, typename AT, typename Epi>
+cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, const Epi& epi,
+                        cudaStream_t st) {
+  if (p->nb == 0) return cudaSuccess;
+  auto kern = merbit_spmv_kernel<VT, XT, AT, Epi>;
+  const size_t smem = 2 * stage_bytes<VT>(p->sigma);
+  int grid = persistent_grid(reinterpret_cast<const void*>(kern), kThreads, smem, p->num_sms);
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  if ((int64_t)grid > p->nb) grid = (int)p->nb;
+  kern<<<grid, kThreads, smem, st>>>(p->geom(), vals, x, epi);
+  return cudaGetLastError();
+}
+
+}  // namespace merbit

@@ -1,0 +1,263 @@
+"""Python binding of libmerbit.so (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts torch
+tensors to device pointers and streams, calls the C ABI declared in
+include/merbit.h and raises MerbitError on a non-OK status.  There is no CPU
+path: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+F32, F64, BF16, F16 = 0, 1, 2, 3
+PLAIN, IR_BF16, IR_F16, IR_F32 = 0, 1, 2, 3
+STATUS = {0: "OK", 1: "EINVAL", 2: "EOVERFLOW", 3: "ENOMEM", 4: "ECUDA", 5: "ENOTCONV",
+          6: "EDEVICE"}
+MODES = {"plain": PLAIN, "ir_bf16": IR_BF16, "ir_f16": IR_F16, "ir_f32": IR_F32}
+_TORCH_DT = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch.float16: F16}
+
+EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_get_info",
+           "merbit_plan_sync", "merbit_plan_export", "merbit_spmv", "merbit_spmv_ex", "merbit_spmv_host",
+           "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_last_error",
+           "merbit_version"]
+
+
+class MerbitError(RuntimeError):
+    def __init__(self, where: str, status: int, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("sigma", ctypes.c_int32), ("omega", ctypes.c_int32),
+                ("tiles_per_block", ctypes.c_int32), ("tile_num", ctypes.c_int64),
+                ("lane_num", ctypes.c_int64), ("block_num", ctypes.c_int64),
+                ("tile_x", ctypes.c_void_p), ("tile_y", ctypes.c_void_p),
+                ("lane_desc", ctypes.c_void_p), ("block_row", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libmerbit.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if path is None:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise MerbitError("load", 4, f"{path} does not exist")
+        lib = ctypes.CDLL(path)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        sig = {
+            "merbit_plan": [vp, vp, i64, i64, ctypes.POINTER(vp)],
+            "merbit_plan_ex": [vp, vp, i64, i64, i64, i32, i32, vp, ctypes.POINTER(vp)],
+            "merbit_plan_get_info": [vp, ctypes.POINTER(PlanInfo)],
+            "merbit_plan_sync": [vp, vp],
+            "merbit_plan_export": [vp, vp, vp, vp, vp],
+            "merbit_spmv": [vp, i32, vp, vp, vp],
+            "merbit_spmv_ex": [vp, i32, i32, vp, vp, vp, i32, vp],
+            "merbit_spmv_host": [vp, i32, vp, vp, vp, vp],
+            "merbit_vals_convert": [vp, i32, vp, i32, i64, i32, ctypes.POINTER(i32), vp],
+            "merbit_pagerank": [vp, i32, vp, dbl, dbl, vp],
+            "merbit_pagerank_ex": [vp, i32, vp, dbl, dbl, i32, i32, i32, vp,
+                                   ctypes.POINTER(i32), ctypes.POINTER(dbl), vp, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = i32
+        lib.merbit_plan_destroy.argtypes = [vp]
+        lib.merbit_plan_destroy.restype = None
+        lib.merbit_last_error.restype = ctypes.c_char_p
+        lib.merbit_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(where: str, status: int, allow: tuple[int, ...] = ()) -> int:
+    if status != 0 and status not in allow:
+        raise MerbitError(where, status, load().merbit_last_error().decode())
+    return status
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to the MERBIT library must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dt(t: torch.Tensor) -> int:
+    try:
+        return _TORCH_DT[t.dtype]
+    except KeyError:
+        raise ValueError(f"unsupported dtype {t.dtype}") from None
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("MERBIT device calls take CUDA tensors")
+
+
+@dataclass
+class TileArrays:
+    tile_x: np.ndarray
+    tile_y: np.ndarray
+    lane_desc: np.ndarray
+    block_row: np.ndarray
+
+
+class Plan:
+    """A reusable MERBIT schedule (TILE arrays + block boundary data) of one CSR pattern.
+
+    The plan borrows ``col_idx``: the tensor is kept referenced here and must
+    not be modified while the plan lives.
+    """
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, n_rows: int | None = None,
+                 n_cols: int | None = None, sigma: int = 14, tiles_per_block: int = 8,
+                 stream=None):
+        lib = load()
+        _need_cuda(row_ptr, col_idx)
+        if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32:
+            raise ValueError("row_ptr and col_idx must be int32")
+        n_rows = row_ptr.numel() - 1 if n_rows is None else n_rows
+        n_cols = n_rows if n_cols is None else n_cols
+        self._col = col_idx
+        self._handle = ctypes.c_void_p()
+        _check("merbit_plan_ex", lib.merbit_plan_ex(_ptr(row_ptr), _ptr(col_idx), n_rows, n_cols,
+                                                   col_idx.numel(), sigma, tiles_per_block,
+                                                   _stream(stream), ctypes.byref(self._handle)))
+        self.n_rows, self.n_cols, self.nnz = n_rows, n_cols, col_idx.numel()
+        self.sigma = sigma
+        self.device = row_ptr.device
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._handle:
+            raise MerbitError("plan", 1, "plan was destroyed")
+        return self._handle
+
+    def info(self) -> PlanInfo:
+        inf = PlanInfo()
+        _check("merbit_plan_get_info", load().merbit_plan_get_info(self.handle, ctypes.byref(inf)))
+        return inf
+
+    def tiles(self) -> TileArrays:
+        """Host copies of the TILE arrays and block rows (merbit_plan_export)."""
+        inf = self.info()
+        t = TileArrays(np.empty(inf.tile_num + 1, np.uint32), np.empty(inf.tile_num + 1, np.uint32),
+                       np.empty(inf.lane_num, np.uint32), np.empty(inf.block_num + 1, np.int32))
+        _check("merbit_plan_export", load().merbit_plan_export(
+            self.handle, *(ctypes.c_void_p(a.ctypes.data) for a in
+                           (t.tile_x, t.tile_y, t.lane_desc, t.block_row))))
+        return t
+
+    def sync(self, stream=None):
+        _check("merbit_plan_sync", load().merbit_plan_sync(self.handle, _stream(stream)))
+
+    def destroy(self):
+        if getattr(self, "_handle", None):
+            load().merbit_plan_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def plan(row_ptr, col_idx, n_rows=None, n_cols=None, sigma=14, stream=None) -> Plan:
+    """merbit_plan: build the reusable TILE schedule of a CSR pattern."""
+    return Plan(row_ptr, col_idx, n_rows, n_cols, sigma=sigma, stream=stream)
+
+
+def spmv(p: Plan, vals: torch.Tensor, x: torch.Tensor, y: torch.Tensor | None = None,
+         scale_exp: int = 0, stream=None) -> torch.Tensor:
+    """merbit_spmv_ex: y = A x (y fully overwritten)."""
+    _need_cuda(vals, x, y)
+    xdt = _dt(x)
+    if y is None:
+        y = torch.empty(p.n_rows, dtype=x.dtype, device=x.device)
+    _check("merbit_spmv_ex", load().merbit_spmv_ex(p.handle, _dt(vals), xdt, _ptr(vals), _ptr(x),
+                                                  _ptr(y), scale_exp, _stream(stream)))
+    return y
+
+
+def spmv_host(p: Plan, vals: torch.Tensor, x_host: torch.Tensor, y_host: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    """merbit_spmv_host: x and y in host memory (pinned recommended); synchronous."""
+    _need_cuda(vals)
+    if x_host.is_cuda:
+        raise ValueError("x_host must be a CPU tensor")
+    if y_host is None:
+        y_host = torch.empty(p.n_rows, dtype=x_host.dtype, pin_memory=True)
+    _check("merbit_spmv_host", load().merbit_spmv_host(p.handle, _dt(vals), _ptr(vals),
+                                                      _ptr(x_host), _ptr(y_host), _stream(stream)))
+    return y_host
+
+
+def vals_convert(src: torch.Tensor, dtype: torch.dtype, auto_scale: bool = False,
+                 stream=None) -> tuple[torch.Tensor, int]:
+    """merbit_vals_convert: round values to bf16 / f16 / f32 (RNE); returns (dst, scale_exp)."""
+    _need_cuda(src)
+    dst = torch.empty(src.numel(), dtype=dtype, device=src.device)
+    k = ctypes.c_int(0)
+    _check("merbit_vals_convert", load().merbit_vals_convert(
+        _ptr(src), _dt(src), _ptr(dst), _TORCH_DT[dtype], src.numel(), int(auto_scale),
+        ctypes.byref(k), _stream(stream)))
+    return dst, k.value
+
+
+def pagerank(p: Plan, vals: torch.Tensor, alpha: float = 0.85, tol: float = 1e-10,
+             max_iter: int = 10000, mode: str = "plain", inner_sweeps: int = 16,
+             pi: torch.Tensor | None = None, stream=None, history: bool = False) -> tuple[torch.Tensor, dict]:
+    """merbit_pagerank_ex.  Returns (pi, info) with info keys iters, resid, converged[, hist]."""
+    _need_cuda(vals, pi)
+    m = MODES[mode]
+    dtype = vals.dtype if m == PLAIN else torch.float64
+    if pi is None:
+        pi = torch.empty(p.n_rows, dtype=dtype, device=vals.device)
+    iters = ctypes.c_int(0)
+    resid = ctypes.c_double(0.0)
+    hist = np.zeros(max_iter + 1, np.float64) if history else None
+    st = _check("merbit_pagerank_ex", load().merbit_pagerank_ex(
+        p.handle, _dt(vals), _ptr(vals), alpha, tol, max_iter, m, inner_sweeps, _ptr(pi),
+        ctypes.byref(iters), ctypes.byref(resid),
+        ctypes.c_void_p(hist.ctypes.data) if history else ctypes.c_void_p(0), _stream(stream)),
+        allow=(5,))
+    info = {"iters": iters.value, "resid": resid.value, "converged": st == 0}
+    if history:
+        n = iters.value if m == PLAIN else iters.value + 1
+        info["hist"] = hist[:n].copy()
+    return pi, info
+
+
+def version() -> str:
+    return load().merbit_version().decode()
