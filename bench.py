@@ -1,0 +1,398 @@
+"""Benchmark of the MERBIT hot path on one GB300 (or N independent replicas).
+
+Workload: the R-MAT scale-24 transition matrix P^T (16,777,216 vertices, edge
+factor 16, a/b/c/d = .57/.19/.19/.05, seed 7, self loops and duplicates
+dropped), synthetic.  One timed step is one FP32 SpMV y = P^T x through the
+plan (built once, outside the timed region, its time reported as plan_ms);
+x ~ U[0,1).  The same run then times PageRank to L1 residual 1e-10 in every
+precision mode, the SpMV through host buffers (e2e) and the CPU oracle on a
+bounded sample (cpu_baseline).
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle
+instead (the reference arm of this project is the float64 oracle).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV Gnnz/s + % HBM roofline; PageRank time to 1e-10, mixed vs plain FP32"
+WORKLOADS = {
+    # name: (scale, edge_factor, seed)
+    "rmat24_transition": (24, 16, 7),
+    "rmat22_transition": (22, 16, 7),
+    "rmat21_transition": (21, 16, 7),
+    "rmat18_transition": (18, 16, 7),
+    "rmat14_transition": (14, 16, 1),
+}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "spmv_f32_rmat24_traffic.txt")
+KERNEL_SOURCES = ["paper_2605_07391_gb300/csrc/spmv_kernel.cuh",
+                  "paper_2605_07391_gb300/csrc/spmv_f32.cu",
+                  "paper_2605_07391_gb300/csrc/merbit_internal.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha") != kernel_hash() or kv.get("workload") != workload:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.6)
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(f[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        lo, hi = (min(self.marks) - 1, max(self.marks) + 1) if self.marks else (-1e18, 1e18)
+        inside = [r for r in rows if lo <= r[0] <= hi] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample_rate(a, budget_s: float, x64: np.ndarray, start_row: int = 0):
+    """Time the oracle's float64 SpMV on contiguous row blocks until budget_s is spent."""
+    import oracle
+
+    nnz_done, t_used, r0 = 0, 0.0, start_row
+    block = max(1, a.n_rows // 64)
+    while t_used < budget_s:
+        r1 = min(a.n_rows, r0 + block)
+        lo, hi = int(a.row_ptr[r0]), int(a.row_ptr[r1])
+        rp = (a.row_ptr[r0:r1 + 1] - lo).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.spmv(rp, a.col[lo:hi], a.val[lo:hi], x64)
+        t_used += time.perf_counter() - t0
+        nnz_done += hi - lo
+        r0 = r1 if r1 < a.n_rows else 0
+    return nnz_done, t_used
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the float64 CPU oracle on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import inputs
+
+    scale, ef, seed = WORKLOADS[args.workload]
+    a = inputs.rmat_transition(scale, ef, seed)
+    x64 = inputs.uniform_vector(a.n_cols, 2)
+    per_step = max(0.01, args.ref_budget / (args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample_rate(a, per_step, x64)
+    nnz_done, t_used, row = 0, 0.0, 0
+    for i in range(args.steps):
+        n_, t_ = oracle_sample_rate(a, per_step, x64, start_row=(i * a.n_rows // 7) % a.n_rows)
+        nnz_done += n_
+        t_used += t_
+    value = nnz_done / t_used / 1e9
+    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "Gnnz/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_used / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "scale": scale, "edge_factor": ef, "seed": seed,
+                       "n": a.n_rows, "nnz": a.nnz, "parallelism": "host cores, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
+                             "sample": f"contiguous row blocks of ~1/64 of the matrix, "
+                                       f"{per_step * 1e3:.0f} ms of oracle SpMV per step"},
+            "e2e": {"value": value, "unit": "Gnnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def algorithmic_bytes_f32(a, tiles) -> tuple[int, dict]:
+    """Algorithmic DRAM bytes of one FP32 SpMV: vals + col (8 m), x and y once (4 n each),
+    descriptors of the non-single-row tiles (4 per lane), tile_x and tile_y (8 per tile)."""
+    marked = (tiles.tile_y[:-1] & 0x80000000) != 0
+    tile_num = tiles.tile_y.size - 1
+    lane_num = tiles.lane_desc.size
+    lanes_in_normal = lane_num - 32 * int(marked.sum())
+    if marked.size and marked[-1]:
+        lanes_in_normal += 32 * tile_num - lane_num     # the last tile may be partial
+    parts = {"vals_col": 8 * a.nnz, "x": 4 * a.n_cols, "y": 4 * a.n_rows,
+             "lane_desc": 4 * max(0, lanes_in_normal), "tile_xy": 8 * (tile_num + 1)}
+    return sum(parts.values()), {"r_f": float(marked.mean()) if marked.size else 0.0, **parts}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="merbit", choices=["merbit", "reference"])
+    ap.add_argument("--workload", default="rmat24_transition", choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work (reference arm)")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work (cpu_baseline)")
+    ap.add_argument("--no-pagerank", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--inner-sweeps", type=int, default=16)
+    args = ap.parse_args()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    import inputs
+    import paper_2605_07391_gb300 as mb
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    mb.load()
+
+    scale, ef, seed = WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    a = inputs.rmat_transition(scale, ef, seed)
+    gen_s = time.perf_counter() - t0
+    x64 = inputs.uniform_vector(a.n_cols, 2)
+    row_ptr = torch.from_numpy(a.row_ptr).to(dev)
+    col = torch.from_numpy(a.col).to(dev)
+    v64 = torch.from_numpy(a.val).to(dev)
+    v32 = v64.float()
+    x = torch.from_numpy(x64).to(dev, torch.float32)
+    y = torch.empty(a.n_rows, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # plan (one-time preprocessing), timed on its own
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    p = mb.plan(row_ptr, col, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    plan_ms = ev0.elapsed_time(ev1)
+    tiles = p.tiles()
+    alg_bytes, alg_parts = algorithmic_bytes_f32(a, tiles)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier(device_ids=[local])
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- timed region: K FP32 SpMV launches (one kernel each)
+    for _ in range(args.warmup):
+        mb.spmv(p, v32, x, y, stream=stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    total0, total1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    clocks.mark()
+    total0.record(stream)
+    for i in range(K):
+        starts[i].record(stream)
+        mb.spmv(p, v32, x, y, stream=stream)
+        ends[i].record(stream)
+    total1.record(stream)
+    barrier()
+    clocks.mark()
+    clock_info = clocks.stop()
+    p.sync(stream)
+    elapsed_ms = max_over_ranks(total0.elapsed_time(total1))
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    mean_launch_ms = statistics.fmean(launch_ms)
+    ms_per_step = elapsed_ms / K
+    value = world * a.nnz / (ms_per_step * 1e-3) / 1e9
+    hbm_peak, peak_kind = peaks()
+    achieved = alg_bytes / (mean_launch_ms * 1e-3) / 1e9
+    traffic = measured_traffic(args.workload)
+
+    out = {"metric": METRIC, "value": value, "unit": "Gnnz/s", "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "scale": scale, "edge_factor": ef, "seed": seed,
+                      "n": a.n_rows, "nnz": a.nnz, "sigma": p.sigma, "omega": 32,
+                      "tiles_per_block": 8, "x": "U[0,1) seed 2",
+                      "l2": f"inputs larger than L2: {(8 * a.nnz + 8 * a.n_rows) / 1e9:.2f} GB read per step",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": achieved / hbm_peak, "traffic": traffic,
+                        "peak_kind": peak_kind,
+                        "algorithmic_bytes_per_launch": alg_bytes,
+                        "bytes_per_nnz": alg_bytes / a.nnz, "parts": alg_parts,
+                        "kernel": "merbit_spmv_kernel<float,float,float,EpiPlain>",
+                        "mean_launch_ms": mean_launch_ms,
+                        "median_launch_ms": statistics.median(launch_ms)},
+           "plan_ms": plan_ms, "gen_s": gen_s, "gpu_launches": K, "clocks": clock_info}
+
+    if rank == 0:
+        # ---- end to end through the host-buffer entry point (pinned buffers)
+        xh = x.cpu().pin_memory()
+        yh = torch.empty(a.n_rows, dtype=torch.float32).pin_memory()
+        for _ in range(3):
+            mb.spmv_host(p, v32, xh, yh, stream=stream)
+        ke = min(K, 50)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            mb.spmv_host(p, v32, xh, yh, stream=stream)
+        e2e_s = (time.perf_counter() - t0) / ke
+        out["e2e"] = {"value": a.nnz / e2e_s / 1e9, "unit": "Gnnz/s", "h2d_bytes_per_step": 4 * a.n_cols,
+                      "d2h_bytes_per_step": 4 * a.n_rows, "ms_per_step": e2e_s * 1e3,
+                      "entry_point": "merbit_spmv_host"}
+
+        # ---- other value types of the same product
+        other = {}
+        lo, k = mb.vals_convert(v64, torch.bfloat16)
+        x64d = x.double()
+        y64 = torch.empty(a.n_rows, dtype=torch.float64, device=dev)
+        for name, fn in (("f64", lambda: mb.spmv(p, v64, x64d, y64, stream=stream)),
+                         ("bf16_vals", lambda: mb.spmv(p, lo, x, y, stream=stream))):
+            for _ in range(5):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(100):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / 100
+            other[name] = {"gnnz_s": a.nnz / (ms * 1e-3) / 1e9, "ms": ms}
+        out["spmv_other"] = other
+        del lo, y64, x64d
+
+        # ---- PageRank to L1 residual 1e-10
+        if not args.no_pagerank:
+            import oracle
+            pr = {}
+            runs = [("ir_bf16", torch.float64), ("ir_f16", torch.float64), ("ir_f32", torch.float64),
+                    ("plain_f64", torch.float64), ("plain_f32", torch.float32)]
+            for name, dt in runs:
+                mode = "plain" if name.startswith("plain") else name
+                vals = v64 if dt == torch.float64 else v32
+                kw = dict(tol=1e-10, max_iter=400 if mode == "plain" else 60, mode=mode,
+                          inner_sweeps=args.inner_sweeps, stream=stream)
+                mb.pagerank(p, vals, 0.85, **dict(kw, max_iter=2, tol=0.0))   # warm
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                pi, info = mb.pagerank(p, vals, 0.85, **kw)
+                torch.cuda.synchronize(dev)
+                ms = (time.perf_counter() - t0) * 1e3
+                rec = {"ms": ms, "iters": info["iters"], "resid": info["resid"],
+                       "converged": info["converged"], "end_to_end_ms": ms + plan_ms}
+                if mode != "plain":
+                    rec["inner_sweeps"] = args.inner_sweeps
+                if not args.no_oracle_check:
+                    pin = pi.double().cpu().numpy()
+                    r = oracle.pagerank_residual(a.row_ptr, a.col, a.val, pin, 0.85)
+                    rec["oracle_l1_residual"] = r
+                    rec["l1_err_bound_vs_fp64_fixed_point"] = r / 0.15
+                pr[name] = rec
+                del pi
+            out["pagerank"] = pr
+            if pr["ir_f32"]["converged"] and pr["ir_bf16"]["converged"]:
+                out["pagerank"]["mixed_vs_ir_f32_speedup"] = pr["ir_f32"]["ms"] / pr["ir_bf16"]["ms"]
+            if pr["plain_f64"]["converged"]:
+                out["pagerank"]["mixed_vs_plain_f64_speedup"] = pr["plain_f64"]["ms"] / pr["ir_bf16"]["ms"]
+
+        # ---- CPU baseline: the float64 oracle on a bounded sample
+        nnz_done, t_used = oracle_sample_rate(a, args.cpu_budget, x64)
+        out["cpu_baseline"] = {"value": nnz_done / t_used / 1e9, "unit": "Gnnz/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"float64 oracle SpMV on contiguous row blocks of ~1/64 of "
+                                         f"the matrix, {nnz_done} nnz in {t_used:.1f} s"}
+        print(json.dumps(out), flush=True)
+    p.destroy()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier(device_ids=[local])
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
