@@ -124,6 +124,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(inside)}
 
 
+def max_over_ranks(v: float, device=None) -> float:
+    """Maximum of a per-rank scalar over the process group (the value itself without one)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gnnz(nnz_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processes nnz_per_rank nonzeros per step."""
+    return world * nnz_per_rank / (ms_per_step * 1e-3) / 1e9
+
+
 def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -255,14 +272,6 @@ def main():
             dist.barrier(device_ids=[local])
         torch.cuda.synchronize(dev)
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     # ---- timed region: K FP32 SpMV launches (one kernel each)
     for _ in range(args.warmup):
         mb.spmv(p, v32, x, y, stream=stream)
@@ -284,11 +293,11 @@ def main():
     clocks.mark()
     clock_info = clocks.stop()
     p.sync(stream)
-    elapsed_ms = max_over_ranks(total0.elapsed_time(total1))
+    elapsed_ms = max_over_ranks(total0.elapsed_time(total1), dev)
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     mean_launch_ms = statistics.fmean(launch_ms)
     ms_per_step = elapsed_ms / K
-    value = world * a.nnz / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_gnnz(a.nnz, world, ms_per_step)
     hbm_peak, peak_kind = peaks()
     achieved = alg_bytes / (mean_launch_ms * 1e-3) / 1e9
     traffic = measured_traffic(args.workload)

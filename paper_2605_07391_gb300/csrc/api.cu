@@ -60,9 +60,8 @@ void free_plan(merbit_plan_s* p) {
   cudaFree(p->lane_desc);
   cudaFree(p->bnd_row);
   cudaFree(p->bnd_slot);
-  cudaFree(p->bnd_expect);
   cudaFree(p->bnd_acc);
-  cudaFree(p->bnd_cnt);
+  cudaFree(p->part);
   cudaFree(p->red);
   cudaFree(p->dangling_bits);
   cudaFree(p->scratch);
@@ -86,7 +85,6 @@ cudaError_t grow(void** buf, size_t* cap, size_t need) {
 cudaError_t reset_device_state(merbit_plan_s* p, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(p->red, 0, sizeof(RedState), st);
   if (e == cudaSuccess && p->nb > 0) e = cudaMemsetAsync(p->bnd_acc, 0, sizeof(double) * (p->nb + 1), st);
-  if (e == cudaSuccess && p->nb > 0) e = cudaMemsetAsync(p->bnd_cnt, 0, sizeof(unsigned) * (p->nb + 1), st);
   return e;
 }
 
@@ -329,9 +327,8 @@ merbit_status merbit_plan_ex(const int32_t* row_ptr, const int32_t* col_idx, int
   if (e == cudaSuccess) e = cudaMalloc(&p->lane_desc, sizeof(uint32_t) * (size_t)std::max<int64_t>(p->lane_num, 1));
   if (e == cudaSuccess) e = cudaMalloc(&p->bnd_row, nbb);
   if (e == cudaSuccess) e = cudaMalloc(&p->bnd_slot, nbb);
-  if (e == cudaSuccess) e = cudaMalloc(&p->bnd_expect, nbb);
   if (e == cudaSuccess) e = cudaMalloc(&p->bnd_acc, sizeof(double) * (size_t)(p->nb + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&p->bnd_cnt, sizeof(unsigned) * (size_t)(p->nb + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->part, sizeof(double2) * (size_t)kMaxParts);
   if (e == cudaSuccess) e = cudaMalloc(&p->red, sizeof(RedState));
   if (e == cudaSuccess) e = cudaMallocHost(&p->host_pinned, 256);
   if (e != cudaSuccess) return bail(cuda_fail(e, "plan allocation"));

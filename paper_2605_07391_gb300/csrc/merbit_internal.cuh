@@ -17,6 +17,7 @@ constexpr int kThreads = kTilesPerBlock * kOmega;   // one warp per tile
 constexpr int kRedSlots = 64;       // spread slots of the grid-wide FP64 reductions
 constexpr uint32_t kMsb = 0x80000000u;
 constexpr uint32_t kSpinLimit = 1u << 22;           // bounded mbarrier waits
+constexpr int kMaxParts = 4096;                     // cap on persistent CTAs (partials array)
 
 // Per-plan device state for grid-wide reductions and kernel-side errors.
 struct RedState {
@@ -34,9 +35,8 @@ struct Geometry {
   const int32_t* col;
   const int32_t* bnd_row;
   const int32_t* bnd_slot;
-  const int32_t* bnd_expect;
   double* bnd_acc;
-  unsigned int* bnd_cnt;
+  double2* part;   // per-CTA reduction partials of the main kernel
   RedState* red;
   int n_rows;
   int nnz;
@@ -61,9 +61,8 @@ struct merbit_plan_s {
   uint32_t* lane_desc = nullptr;
   int32_t* bnd_row = nullptr;
   int32_t* bnd_slot = nullptr;
-  int32_t* bnd_expect = nullptr;
   double* bnd_acc = nullptr;
-  unsigned int* bnd_cnt = nullptr;
+  double2* part = nullptr;               // kMaxParts entries
   merbit::RedState* red = nullptr;
   // lazily built PageRank data
   uint32_t* dangling_bits = nullptr;     // (n+31)/32 words, bit set = dangling vertex
@@ -81,8 +80,8 @@ struct merbit_plan_s {
   merbit::Geometry geom() const {
     merbit::Geometry g;
     g.tile_x = tile_x; g.tile_y = tile_y; g.lane_desc = lane_desc; g.col = col;
-    g.bnd_row = bnd_row; g.bnd_slot = bnd_slot; g.bnd_expect = bnd_expect;
-    g.bnd_acc = bnd_acc; g.bnd_cnt = bnd_cnt; g.red = red;
+    g.bnd_row = bnd_row; g.bnd_slot = bnd_slot;
+    g.bnd_acc = bnd_acc; g.part = part; g.red = red;
     g.n_rows = (int)n_rows; g.nnz = (int)nnz; g.steps = (int)(nnz + n_rows);
     g.sigma = sigma; g.tile_num = (int)tile_num; g.lane_num = (int)lane_num; g.nb = (int)nb;
     return g;

@@ -98,17 +98,6 @@ __global__ void plan_slots_kernel(const int32_t* __restrict__ bnd_row, int nb,
   bnd_slot[b] = lo;
 }
 
-// Arrivals per boundary slot: block v contributes its first row, and its last
-// row when that row differs from the first and exists.
-__global__ void plan_expect_kernel(const int32_t* __restrict__ bnd_row,
-                                   const int32_t* __restrict__ bnd_slot, int nb, int n_rows,
-                                   int32_t* __restrict__ expect) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nb) return;
-  atomicAdd(expect + bnd_slot[v], 1);
-  if (bnd_row[v + 1] != bnd_row[v] && bnd_row[v + 1] < n_rows) atomicAdd(expect + bnd_slot[v + 1], 1);
-}
-
 __global__ void mark_columns_kernel(const int32_t* __restrict__ col, int nnz,
                                     uint8_t* __restrict__ present) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x)
@@ -144,10 +133,6 @@ cudaError_t build_tiles(const merbit_plan_s* p, const int32_t* row_ptr, cudaStre
   plan_block_rows_kernel<<<nbt, threads, 0, st>>>(p->tile_y, (int)p->tile_num, p->tiles_per_block,
                                                   (int)p->nb, p->bnd_row);
   plan_slots_kernel<<<nbt, threads, 0, st>>>(p->bnd_row, (int)p->nb, p->bnd_slot);
-  e = cudaMemsetAsync(p->bnd_expect, 0, sizeof(int32_t) * (p->nb + 1), st);
-  if (e != cudaSuccess) return e;
-  plan_expect_kernel<<<nbt, threads, 0, st>>>(p->bnd_row, p->bnd_slot, (int)p->nb, (int)p->n_rows,
-                                              p->bnd_expect);
   return cudaGetLastError();
 }
 

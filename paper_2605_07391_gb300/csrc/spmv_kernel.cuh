@@ -16,12 +16,14 @@
 //     stage holds W*omega*sigma + 16 elements of each array (Sec. 4.3's
 //     (b+1)*sigma bound, re-derived for this layout);
 //   * rows shared between blocks (the block's first and last row) are added
-//     into per-row FP64 accumulators; the last CTA to arrive at a row (counted
-//     against the arrival count fixed by the plan) finalises it and clears
-//     the accumulator, so outputs are written exactly once and no vector
-//     ever needs clearing between calls (the role of the paper's dual-buffer
-//     commit, which resets only block-boundary rows).
+//     into per-row FP64 accumulators with fire-and-forget atomics; a small
+//     second kernel writes those rows, clears the accumulators and finishes the
+//     grid-wide FP64 reductions, so outputs are written exactly once and no
+//     vector ever needs clearing between calls (the role of the paper's
+//     dual-buffer commit, which resets only block-boundary rows).
 #pragma once
+
+#include <algorithm>
 
 #include "merbit_internal.cuh"
 
@@ -288,7 +290,7 @@ struct ProdInVals {
 };
 
 template <typename VT, typename XT, typename AT, typename Epi>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
     merbit_spmv_kernel(const Geometry g, const VT* __restrict__ vals, const XT* __restrict__ x,
                        Epi epi) {
   static_assert(ProdInVals<VT, AT>::value || sizeof(AT) == 4, "product slot width");
@@ -395,26 +397,25 @@ __global__ void __launch_bounds__(kThreads, 2)
     // ---- stage products val * x[col] (load_smem of Algorithm MERBIT SpMV)
     {
       const int cnt = in.x_be - in.x_bs;
-      int cidx[kSigmaMax];
-      AT vv[kSigmaMax];
-#pragma unroll
-      for (int u = 0; u < kSigmaMax; ++u) {
-        const int k = in.x_bs + tid + u * kThreads;
-        cidx[u] = 0;
-        vv[u] = AT(0);
-        if (tid + u * kThreads < cnt) {
-          cidx[u] = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
-          vv[u] = static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
-        }
-      }
       AT xv[kSigmaMax];
 #pragma unroll
-      for (int u = 0; u < kSigmaMax; ++u)
-        xv[u] = (tid + u * kThreads < cnt) ? static_cast<AT>(ld_x(x + cidx[u], pol_x)) : AT(0);
+      for (int u = 0; u < kSigmaMax; ++u) {
+        const int e = tid + u * kThreads;
+        xv[u] = AT(0);
+        if (e < cnt) {
+          const int k = in.x_bs + e;
+          const int c = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
+          xv[u] = static_cast<AT>(ld_x(x + c, pol_x));
+        }
+      }
 #pragma unroll
       for (int u = 0; u < kSigmaMax; ++u) {
-        const int k = in.x_bs + tid + u * kThreads;
-        if (tid + u * kThreads < cnt) prod[k - pb] = vv[u] * xv[u];
+        const int e = tid + u * kThreads;
+        if (e < cnt) {
+          const int k = in.x_bs + e;
+          const AT v = static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
+          prod[k - pb] = v * xv[u];
+        }
       }
     }
     AT* s_y = prod + (in.x_be - pb);
@@ -486,23 +487,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     // ---- block commit: interior rows complete here, boundary rows via FP64 accumulators
     for (int r = in.y_bs + 1 + tid; r < in.y_be; r += kThreads) epi.row(r, s_y[r - in.y_bs], p0, p1);
-    if ((tid & 31) == 0 && tid < 64) {
-      const int which = tid >> 5;
-      const int r = which ? in.y_be : in.y_bs;
-      const bool contributes = which == 0 || (in.y_be != in.y_bs && in.y_be < g.n_rows);
-      if (contributes) {
-        const int slot = __ldg(g.bnd_slot + v + which);
-        atomicAdd(g.bnd_acc + slot, static_cast<double>(s_y[r - in.y_bs]));
-        __threadfence();
-        const unsigned int t = atomicAdd(g.bnd_cnt + slot, 1u);
-        if (t + 1 == (unsigned int)__ldg(g.bnd_expect + slot)) {
-          __threadfence();
-          const double tot = read_reset(g.bnd_acc + slot);
-          g.bnd_cnt[slot] = 0u;
-          epi.row64(r, tot, p0, p1);
-        }
-      }
-    }
+    if (tid == 0) atomicAdd(g.bnd_acc + __ldg(g.bnd_slot + v), static_cast<double>(s_y[0]));
+    if (tid == 32 && in.y_be != in.y_bs && in.y_be < g.n_rows)
+      atomicAdd(g.bnd_acc + __ldg(g.bnd_slot + v + 1), static_cast<double>(s_y[in.y_be - in.y_bs]));
     // stage s is free again once every thread is past this point
     fence_proxy_async_smem();
     __syncthreads();
@@ -524,13 +511,60 @@ __global__ void __launch_bounds__(kThreads, 2)
         a += red_smem[w][0];
         b += red_smem[w][1];
       }
+      g.part[blockIdx.x] = make_double2(a, b);
+    }
+  }
+}
+
+// Second pass: rows shared between blocks (one thread per distinct boundary
+// row: the FP64 total of its accumulator goes through the epilogue, and the
+// accumulator is cleared), then the grid-wide FP64 reductions: per-CTA
+// partials of both kernels are summed by the last CTA of this kernel.
+template <typename Epi>
+__global__ void __launch_bounds__(256) merbit_finalize_kernel(const Geometry g, Epi epi,
+                                                              int nparts) {
+  __shared__ double red_smem[8][2];
+  __shared__ bool last;
+  if (epi.skip(g.red)) return;
+  epi.init();
+  double p0 = 0.0, p1 = 0.0;
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int k = t0; k <= g.nb; k += stride) {
+    if (__ldg(g.bnd_slot + k) != k) continue;
+    const int r = __ldg(g.bnd_row + k);
+    if (r >= g.n_rows) continue;
+    const double tot = g.bnd_acc[k];
+    g.bnd_acc[k] = 0.0;
+    epi.row64(r, tot, p0, p1);
+  }
+  if constexpr (Epi::kReduce) {
+    for (int i = t0; i < nparts; i += stride) {
+      const double2 q = g.part[i];
+      p0 += q.x;
+      p1 += q.y;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    p0 = warp_sum(p0);
+    p1 = warp_sum(p1);
+    if (lane == 0) {
+      red_smem[warp][0] = p0;
+      red_smem[warp][1] = p1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+        a += red_smem[w][0];
+        b += red_smem[w][1];
+      }
       RedState* red = g.red;
       const int q = blockIdx.x % kRedSlots;
       atomicAdd(&red->slot[q][0], a);
       atomicAdd(&red->slot[q][1], b);
       __threadfence();
-      const unsigned int t = atomicAdd(&red->arrive, 1u);
-      if (t + 1 == gridDim.x) {
+      last = atomicAdd(&red->arrive, 1u) + 1 == gridDim.x;
+      if (last) {
         __threadfence();
         double A = 0.0, B = 0.0;
         for (int i = 0; i < kRedSlots; ++i) {
@@ -553,7 +587,12 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   int grid = persistent_grid(reinterpret_cast<const void*>(kern), kThreads, smem, p->num_sms);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   if ((int64_t)grid > p->nb) grid = (int)p->nb;
+  if (grid > kMaxParts) grid = kMaxParts;
   kern<<<grid, kThreads, smem, st>>>(p->geom(), vals, x, epi);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int fgrid = (int)std::min<int64_t>((p->nb + 1 + 255) / 256, (int64_t)p->num_sms * 4);
+  merbit_finalize_kernel<Epi><<<fgrid, 256, 0, st>>>(p->geom(), epi, Epi::kReduce ? grid : 0);
   return cudaGetLastError();
 }
 
