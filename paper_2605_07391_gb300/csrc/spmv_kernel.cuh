@@ -259,13 +259,23 @@ struct EpiSweep {
 
 struct StageInfo {
   int x_bs, x_be, y_bs, y_be;   // block start / end coordinates
-  int a0v, endv;                // values staged for [a0v, endv)
-  int a0c, endc;                // column indices staged for [a0c, endc)
+  int a0, end;                  // values and column indices staged for [a0, end)
 };
+
+// Both staged arrays start at a multiple of A elements, so that 16 bytes of
+// values and of column indices are 16-byte aligned (bulk-copy rule) and groups
+// of 4 elements can be moved with vector shared-memory accesses.
+template <typename VT>
+__host__ __device__ constexpr int stage_align() {
+  return (16 / (int)sizeof(VT)) > 4 ? 16 / (int)sizeof(VT) : 4;
+}
+
+constexpr int kStagePad = 32;
+constexpr int kGroupIters = (kThreads * kSigmaMax + kStagePad) / 4 / kThreads + 1;
 
 template <typename VT>
 __host__ __device__ constexpr int stage_cap(int sigma) {
-  return kThreads * sigma + 16;
+  return kThreads * sigma + kStagePad;
 }
 
 __host__ __device__ inline size_t round128(size_t b) { return (b + 127) & ~size_t(127); }
@@ -289,12 +299,42 @@ struct ProdInVals {
   static constexpr bool value = sizeof(VT) == sizeof(AT);
 };
 
+// 4 staged values of group gi, widened to the accumulator type.
+__device__ __forceinline__ void load4(const float* s, int gi, float (&v)[4]) {
+  const float4 t = reinterpret_cast<const float4*>(s)[gi];
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* s, int gi, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(s)[2 * gi];
+  const double2 b = reinterpret_cast<const double2*>(s)[2 * gi + 1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* s, int gi, float (&v)[4]) {
+  // a bf16 is the upper half of the f32 with the same value
+  const uint2 t = reinterpret_cast<const uint2*>(s)[gi];
+  v[0] = __uint_as_float(t.x << 16); v[1] = __uint_as_float(t.x & 0xffff0000u);
+  v[2] = __uint_as_float(t.y << 16); v[3] = __uint_as_float(t.y & 0xffff0000u);
+}
+__device__ __forceinline__ void load4(const __half* s, int gi, float (&v)[4]) {
+  const uint2 t = reinterpret_cast<const uint2*>(s)[gi];
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&t.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&t.y));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void store4(float* p, int gi, const float (&v)[4]) {
+  reinterpret_cast<float4*>(p)[gi] = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, int gi, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[2 * gi] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[2 * gi + 1] = make_double2(v[2], v[3]);
+}
+
 template <typename VT, typename XT, typename AT, typename Epi>
 __global__ void __launch_bounds__(kThreads, 3)
     merbit_spmv_kernel(const Geometry g, const VT* __restrict__ vals, const XT* __restrict__ x,
                        Epi epi) {
   static_assert(ProdInVals<VT, AT>::value || sizeof(AT) == 4, "product slot width");
-  constexpr int VE = 16 / (int)sizeof(VT);   // values per 16 bytes
+  constexpr int A = stage_align<VT>();
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ StageInfo info[2];
   __shared__ double red_smem[kThreads / 32][2];
@@ -314,8 +354,7 @@ __global__ void __launch_bounds__(kThreads, 3)
 
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_x = policy_evict_last();
-  const int nnz_v = g.nnz & ~(VE - 1);
-  const int nnz_c = g.nnz & ~3;
+  const int nnz_a = g.nnz & ~(A - 1);
 
   // geometry of block v, as needed to issue its copies (thread 0 only)
   auto geom_of = [&](int v, int& xb, int& xe, uint32_t& yb, uint32_t& ye) {
@@ -329,16 +368,15 @@ __global__ void __launch_bounds__(kThreads, 3)
   auto issue = [&](int s, int xb, int xe, uint32_t yb, uint32_t ye) {
     StageInfo in;
     in.x_bs = xb; in.x_be = xe; in.y_bs = (int)yb; in.y_be = (int)ye;
-    in.a0v = xb & ~(VE - 1);
-    in.endv = max(in.a0v, min((xe + VE - 1) & ~(VE - 1), nnz_v));
-    in.a0c = xb & ~3;
-    in.endc = max(in.a0c, min((xe + 3) & ~3, nnz_c));
+    in.a0 = xb & ~(A - 1);
+    in.end = max(in.a0, min((xe + A - 1) & ~(A - 1), nnz_a));
     info[s] = in;
-    const uint32_t bv = (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT);
-    const uint32_t bc = (uint32_t)(in.endc - in.a0c) * 4u;
-    mbar_arrive_expect_tx(&mbar[s], bv + bc);
-    if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, &mbar[s], pol_stream);
-    if (bc) bulk_g2s(sc(s), g.col + in.a0c, bc, &mbar[s], pol_stream);
+    const uint32_t cnt = (uint32_t)(in.end - in.a0);
+    mbar_arrive_expect_tx(&mbar[s], cnt * (uint32_t)(sizeof(VT) + sizeof(int32_t)));
+    if (cnt) {
+      bulk_g2s(sv(s), vals + in.a0, cnt * (uint32_t)sizeof(VT), &mbar[s], pol_stream);
+      bulk_g2s(sc(s), g.col + in.a0, cnt * 4u, &mbar[s], pol_stream);
+    }
   };
 
   if (tid == 0) {
@@ -385,40 +423,51 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
     const StageInfo in = info[s];
     AT* prod;
-    int pb;
-    if constexpr (ProdInVals<VT, AT>::value) {
+    if constexpr (ProdInVals<VT, AT>::value)
       prod = reinterpret_cast<AT*>(sv(s));
-      pb = in.a0v;
-    } else {
+    else
       prod = reinterpret_cast<AT*>(sc(s));
-      pb = in.a0c;
-    }
 
-    // ---- stage products val * x[col] (load_smem of Algorithm MERBIT SpMV)
-    {
-      const int cnt = in.x_be - in.x_bs;
-      AT xv[kSigmaMax];
+    // ---- stage products val * x[col] in place (load_smem of Algorithm MERBIT SpMV),
+    //      in groups of 4 staged elements starting at a0
+    const int ng = (in.x_be - in.a0 + 3) >> 2;
+    if (in.a0 + 4 * ng <= in.end) {
+      // every group is fully staged: no per-element checks.  Elements of the
+      // first and last group outside [x_bs, x_be) are real neighbouring
+      // nonzeros; their products land in slots nobody reads.
+      AT xv[kGroupIters][4];
 #pragma unroll
-      for (int u = 0; u < kSigmaMax; ++u) {
-        const int e = tid + u * kThreads;
-        xv[u] = AT(0);
-        if (e < cnt) {
-          const int k = in.x_bs + e;
-          const int c = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
-          xv[u] = static_cast<AT>(ld_x(x + c, pol_x));
+      for (int u = 0; u < kGroupIters; ++u) {
+        const int gi = tid + u * kThreads;
+        if (gi < ng) {
+          const int4 c = reinterpret_cast<const int4*>(sc(s))[gi];
+          xv[u][0] = static_cast<AT>(ld_x(x + c.x, pol_x));
+          xv[u][1] = static_cast<AT>(ld_x(x + c.y, pol_x));
+          xv[u][2] = static_cast<AT>(ld_x(x + c.z, pol_x));
+          xv[u][3] = static_cast<AT>(ld_x(x + c.w, pol_x));
         }
       }
 #pragma unroll
-      for (int u = 0; u < kSigmaMax; ++u) {
-        const int e = tid + u * kThreads;
-        if (e < cnt) {
-          const int k = in.x_bs + e;
-          const AT v = static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
-          prod[k - pb] = v * xv[u];
+      for (int u = 0; u < kGroupIters; ++u) {
+        const int gi = tid + u * kThreads;
+        if (gi < ng) {
+          AT w[4];
+          load4(sv(s), gi, w);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) w[q] *= xv[u][q];
+          store4(prod, gi, w);
         }
+      }
+    } else {
+      // the array's last elements are not staged: element-wise, with global loads
+      for (int e = in.x_bs - in.a0 + tid; e < in.x_be - in.a0; e += kThreads) {
+        const int k = in.a0 + e;
+        const int c = k < in.end ? sc(s)[e] : __ldg(g.col + k);
+        const AT w = static_cast<AT>(widen(k < in.end ? sv(s)[e] : vals[k]));
+        prod[e] = w * static_cast<AT>(ld_x(x + c, pol_x));
       }
     }
-    AT* s_y = prod + (in.x_be - pb);
+    AT* s_y = prod + ((4 * ng + A - 1) & ~(A - 1));
     for (int r = tid; r <= in.y_be - in.y_bs; r += kThreads) s_y[r] = AT(0);
     __syncthreads();
 
@@ -426,42 +475,46 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (tile_ok && txs < txe) {
       const int y_ws = (int)(tys & ~kMsb);
       AT* sy = s_y + (y_ws - in.y_bs);
-      const AT* pt = prod + ((int)txs - pb);
+      const AT* pt = prod + ((int)txs - in.a0);
       if (tys & kMsb) {
         // single-row tile: plain warp reduction, no descriptor
         AT sum = AT(0);
-        for (int k = lane; k < (int)(txe - txs); k += 32) sum += pt[k];
+        const int len = (int)(txe - txs);
+#pragma unroll
+        for (int q = 0; q < kSigmaMax; ++q) {
+          const int k = lane + 32 * q;
+          if (k < len) sum += pt[k];
+        }
+        for (int k = lane + 32 * kSigmaMax; k < len; k += 32) sum += pt[k];
         sum = warp_sum(sum);
         if (lane == 0) atomicAdd(sy, sum);
       } else {
         const bool active = j < g.lane_num;
         const int lane_len = active ? min(g.sigma, g.steps - j * g.sigma) : 0;
+        const uint32_t valid = (1u << lane_len) - 1u;
+        const uint32_t dm = (desc >> 18) & valid;     // down steps
+        const uint32_t rm = ~(desc >> 18) & valid;    // right steps
         int xo = (int)(desc & 511u);
         int yo = active ? (int)((desc >> 9) & 511u) : (g.n_rows - y_ws);
-        const uint32_t fl = desc >> 18;
         AT sum = AT(0);
         bool first = true;
-        bool head = lane == 0;
 #pragma unroll
         for (int k = 0; k < kSigmaMax; ++k) {
-          if (k < lane_len) {
-            if ((fl >> k) & 1u) {
-              // down step: the row in progress ends inside this lane
-              if (first) {
-                atomicAdd(sy + yo, sum);   // the row may have begun in earlier lanes
-                first = false;
-              } else {
-                sy[yo] = sum;              // the row lies entirely in this lane
-              }
-              sum = AT(0);
-              ++yo;
-              head = true;
-            } else {
-              sum += pt[xo];
-              ++xo;
-            }
+          const uint32_t d = (dm >> k) & 1u;
+          const uint32_t rr = (rm >> k) & 1u;
+          const AT pv = pt[xo];
+          if (d) {
+            // down step: the row in progress ends inside this lane; it may have
+            // begun in earlier lanes only if this is the lane's first down step
+            if (first) atomicAdd(sy + yo, sum);
+            else sy[yo] = sum;
+            first = false;
           }
+          sum = d ? AT(0) : (rr ? sum + pv : sum);
+          xo += (int)rr;
+          yo += (int)d;
         }
+        const bool head = lane == 0 || dm != 0u;
         // segmented inclusive scan of trailing sums; heads start segments
         AT sv_ = sum;
         int f = head ? 1 : 0;
