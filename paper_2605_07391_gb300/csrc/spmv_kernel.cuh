@@ -329,14 +329,21 @@ __device__ __forceinline__ void store4(double* p, int gi, const double (&v)[4]) 
   reinterpret_cast<double2*>(p)[2 * gi + 1] = make_double2(v[2], v[3]);
 }
 
+constexpr int kStages = 3;
+
+// Per-warp tile metadata, loaded one block ahead.
+struct TileMeta {
+  uint32_t txs, txe, tys, desc;
+};
+
 template <typename VT, typename XT, typename AT, typename Epi>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 2)
     merbit_spmv_kernel(const Geometry g, const VT* __restrict__ vals, const XT* __restrict__ x,
                        Epi epi) {
   static_assert(ProdInVals<VT, AT>::value || sizeof(AT) == 4, "product slot width");
   constexpr int A = stage_align<VT>();
-  __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ StageInfo info[2];
+  __shared__ __align__(8) uint64_t mbar[kStages];
+  __shared__ StageInfo info[kStages];
   __shared__ double red_smem[kThreads / 32][2];
   extern __shared__ __align__(128) unsigned char dyn_smem[];
 
@@ -351,6 +358,12 @@ __global__ void __launch_bounds__(kThreads, 3)
   const size_t stb = stage_bytes<VT>(g.sigma);
   auto sv = [&](int s) { return reinterpret_cast<VT*>(dyn_smem + (size_t)s * stb); };
   auto sc = [&](int s) { return reinterpret_cast<int32_t*>(dyn_smem + (size_t)s * stb + svb); };
+  auto prod_of = [&](int s) {
+    if constexpr (ProdInVals<VT, AT>::value)
+      return reinterpret_cast<AT*>(sv(s));
+    else
+      return reinterpret_cast<AT*>(sc(s));
+  };
 
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_x = policy_evict_last();
@@ -378,64 +391,28 @@ __global__ void __launch_bounds__(kThreads, 3)
       bulk_g2s(sc(s), g.col + in.a0, cnt * 4u, &mbar[s], pol_stream);
     }
   };
-
-  if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int xb, xe; uint32_t yb, ye;
-    if (blockIdx.x < g.nb) { geom_of(blockIdx.x, xb, xe, yb, ye); issue(0, xb, xe, yb, ye); }
-    if (blockIdx.x + G < g.nb) { geom_of(blockIdx.x + G, xb, xe, yb, ye); issue(1, xb, xe, yb, ye); }
-  }
-
-  double p0 = 0.0, p1 = 0.0;
-  int it = 0;
-  for (int v = blockIdx.x; v < g.nb; v += G, ++it) {
-    const int s = it & 1;
-    const uint32_t par = (it >> 1) & 1;
-
-    // tile metadata of this warp, loaded before the wait to hide latency
+  auto meta_of = [&](int v) {
+    TileMeta m{0u, 0u, 0u, 0u};
     const int ti = v * kTilesPerBlock + warp;
-    const bool tile_ok = ti < g.tile_num;
-    uint32_t txs = 0, txe = 0, tys = 0, desc = 0;
-    const int j = ti * kOmega + lane;
-    if (tile_ok) {
-      txs = __ldg(g.tile_x + ti);
-      txe = __ldg(g.tile_x + ti + 1);
-      tys = __ldg(g.tile_y + ti);
-      if (!(tys & kMsb) && j < g.lane_num) desc = __ldg(g.lane_desc + j);
+    if (v < g.nb && ti < g.tile_num) {
+      m.txs = __ldg(g.tile_x + ti);
+      m.txe = __ldg(g.tile_x + ti + 1);
+      m.tys = __ldg(g.tile_y + ti);
+      const int j = ti * kOmega + lane;
+      if (!(m.tys & kMsb) && j < g.lane_num) m.desc = __ldg(g.lane_desc + j);
     }
-    // geometry for the copy issued at the end of this iteration
-    int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
-    const bool refill = (tid == 0) && (v + 2 * G < g.nb);
-    if (refill) geom_of(v + 2 * G, nxb, nxe, nyb, nye);
+    return m;
+  };
 
-    const bool ok = mbar_wait_bounded(&mbar[s], par);
-    if (__syncthreads_or(!ok)) {
-      // expired wait: record it, let this CTA's copies land (bounded), leave
-      if (tid == 0) atomicOr(&g.red->err, 1);
-      mbar_wait_bounded(&mbar[s], par);
-      if (v + G < g.nb) mbar_wait_bounded(&mbar[s ^ 1], ((it + 1) >> 1) & 1);
-      return;
-    }
-    const StageInfo in = info[s];
-    AT* prod;
-    if constexpr (ProdInVals<VT, AT>::value)
-      prod = reinterpret_cast<AT*>(sv(s));
-    else
-      prod = reinterpret_cast<AT*>(sc(s));
-
-    // ---- stage products val * x[col] in place (load_smem of Algorithm MERBIT SpMV),
-    //      in groups of 4 staged elements starting at a0
+  // x gathers of a staged block, in groups of 4 staged elements from a0
+  // (issued early; consumed by multiply() one phase later)
+  AT xv[kGroupIters][4];
+  auto gather = [&](int s) {
+    const StageInfo& in = info[s];
     const int ng = (in.x_be - in.a0 + 3) >> 2;
     if (in.a0 + 4 * ng <= in.end) {
-      // every group is fully staged: no per-element checks.  Elements of the
-      // first and last group outside [x_bs, x_be) are real neighbouring
-      // nonzeros; their products land in slots nobody reads.
-      AT xv[kGroupIters][4];
+      // every group fully staged; elements of the first / last group outside
+      // [x_bs, x_be) are real neighbouring nonzeros whose products nobody reads
 #pragma unroll
       for (int u = 0; u < kGroupIters; ++u) {
         const int gi = tid + u * kThreads;
@@ -447,6 +424,14 @@ __global__ void __launch_bounds__(kThreads, 3)
           xv[u][3] = static_cast<AT>(ld_x(x + c.w, pol_x));
         }
       }
+    }
+  };
+  // products val * x[col] written over the staged data, then the block's row buffer cleared
+  auto multiply = [&](int s) {
+    const StageInfo& in = info[s];
+    AT* prod = prod_of(s);
+    const int ng = (in.x_be - in.a0 + 3) >> 2;
+    if (in.a0 + 4 * ng <= in.end) {
 #pragma unroll
       for (int u = 0; u < kGroupIters; ++u) {
         const int gi = tid + u * kThreads;
@@ -469,17 +454,81 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
     AT* s_y = prod + ((4 * ng + A - 1) & ~(A - 1));
     for (int r = tid; r <= in.y_be - in.y_bs; r += kThreads) s_y[r] = AT(0);
-    __syncthreads();
+  };
+  auto s_y_of = [&](int s) {
+    const StageInfo& in = info[s];
+    const int ng = (in.x_be - in.a0 + 3) >> 2;
+    return prod_of(s) + ((4 * ng + A - 1) & ~(A - 1));
+  };
+  // bounded wait; on expiry the thread records the error and stops touching staged data
+  bool dead = false;
+  auto wait_stage = [&](int s, int use) {
+    if (!dead && !mbar_wait_bounded(&mbar[s], (uint32_t)(use & 1))) {
+      dead = true;
+      atomicOr(&g.red->err, 1);
+    }
+  };
 
-    // ---- per-tile reduction (tile_fast_tackle / tile_normal_tackle + WarpSegmentedSum)
-    if (tile_ok && txs < txe) {
-      const int y_ws = (int)(tys & ~kMsb);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&mbar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int v0 = blockIdx.x;
+  if (tid == 0) {
+    int xb, xe; uint32_t yb, ye;
+    for (int s = 0; s < kStages; ++s)
+      if (v0 + s * G < g.nb) { geom_of(v0 + s * G, xb, xe, yb, ye); issue(s, xb, xe, yb, ye); }
+  }
+  TileMeta meta = meta_of(v0);
+  // products of the first block
+  wait_stage(0, 0);
+  if (!dead) { gather(0); multiply(0); }
+  fence_proxy_async_smem();
+  bool failed = __syncthreads_or(dead);
+  // block b of this CTA (b = 0, 1, ...) is v0 + b*G, staged in stage b % kStages for the
+  // (b / kStages)-th time; after a failure, wait (bounded) for the copies of blocks lo..hi
+  auto drain = [&](int lo, int hi) {
+    for (int b = lo; b <= hi; ++b)
+      if (v0 + b * G < g.nb) mbar_wait_bounded(&mbar[b % kStages], (uint32_t)((b / kStages) & 1));
+  };
+  if (failed) {
+    drain(0, kStages - 1);
+    return;
+  }
+
+  double p0 = 0.0, p1 = 0.0;
+  int it = 0;
+  for (int v = v0; v < g.nb; v += G, ++it) {
+    const int s = it % kStages;
+    const int s1 = (it + 1) % kStages;
+    const int vn = v + G;
+    const TileMeta cur = meta;
+    meta = meta_of(vn);                       // next block's tile metadata
+    int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
+    const bool refill = (tid == 0) && (v + kStages * G < g.nb);
+    if (refill) geom_of(v + kStages * G, nxb, nxe, nyb, nye);
+
+    // 1. x gathers of the next block go out before this block is reduced
+    if (vn < g.nb) {
+      wait_stage(s1, (it + 1) / kStages);
+      if (!dead) gather(s1);
+    }
+
+    // 2. per-tile reduction of block v (tile_fast_tackle / tile_normal_tackle + WarpSegmentedSum)
+    const StageInfo in = info[s];
+    AT* s_y = s_y_of(s);
+    const AT* prod = prod_of(s);
+    const int ti = v * kTilesPerBlock + warp;
+    const int j = ti * kOmega + lane;
+    if (ti < g.tile_num && cur.txs < cur.txe) {
+      const int y_ws = (int)(cur.tys & ~kMsb);
       AT* sy = s_y + (y_ws - in.y_bs);
-      const AT* pt = prod + ((int)txs - in.a0);
-      if (tys & kMsb) {
+      const AT* pt = prod + ((int)cur.txs - in.a0);
+      if (cur.tys & kMsb) {
         // single-row tile: plain warp reduction, no descriptor
         AT sum = AT(0);
-        const int len = (int)(txe - txs);
+        const int len = (int)(cur.txe - cur.txs);
 #pragma unroll
         for (int q = 0; q < kSigmaMax; ++q) {
           const int k = lane + 32 * q;
@@ -492,10 +541,10 @@ __global__ void __launch_bounds__(kThreads, 3)
         const bool active = j < g.lane_num;
         const int lane_len = active ? min(g.sigma, g.steps - j * g.sigma) : 0;
         const uint32_t valid = (1u << lane_len) - 1u;
-        const uint32_t dm = (desc >> 18) & valid;     // down steps
-        const uint32_t rm = ~(desc >> 18) & valid;    // right steps
-        int xo = (int)(desc & 511u);
-        int yo = active ? (int)((desc >> 9) & 511u) : (g.n_rows - y_ws);
+        const uint32_t dm = (cur.desc >> 18) & valid;     // down steps
+        const uint32_t rm = ~(cur.desc >> 18) & valid;    // right steps
+        int xo = (int)(cur.desc & 511u);
+        int yo = active ? (int)((cur.desc >> 9) & 511u) : (g.n_rows - y_ws);
         AT sum = AT(0);
         bool first = true;
 #pragma unroll
@@ -538,14 +587,21 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
     __syncthreads();
 
-    // ---- block commit: interior rows complete here, boundary rows via FP64 accumulators
+    // 3. block commit: interior rows complete here, boundary rows via FP64 accumulators
     for (int r = in.y_bs + 1 + tid; r < in.y_be; r += kThreads) epi.row(r, s_y[r - in.y_bs], p0, p1);
     if (tid == 0) atomicAdd(g.bnd_acc + __ldg(g.bnd_slot + v), static_cast<double>(s_y[0]));
     if (tid == 32 && in.y_be != in.y_bs && in.y_be < g.n_rows)
       atomicAdd(g.bnd_acc + __ldg(g.bnd_slot + v + 1), static_cast<double>(s_y[in.y_be - in.y_bs]));
-    // stage s is free again once every thread is past this point
+
+    // 4. products of the next block (its gathers have had phases 2-3 to arrive)
+    if (vn < g.nb && !dead) multiply(s1);
+    // stage s is free again, and the next block's products visible, past this point
     fence_proxy_async_smem();
-    __syncthreads();
+    if (__syncthreads_or(dead)) {
+      // an expired wait: blocks it+1 and it+2 may still have copies in flight
+      drain(it + 1, it + 2);
+      return;
+    }
     if (refill) issue(s, nxb, nxe, nyb, nye);
   }
 
@@ -636,7 +692,7 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
                         cudaStream_t st) {
   if (p->nb == 0) return cudaSuccess;
   auto kern = merbit_spmv_kernel<VT, XT, AT, Epi>;
-  const size_t smem = 2 * stage_bytes<VT>(p->sigma);
+  const size_t smem = kStages * stage_bytes<VT>(p->sigma);
   int grid = persistent_grid(reinterpret_cast<const void*>(kern), kThreads, smem, p->num_sms);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   if ((int64_t)grid > p->nb) grid = (int)p->nb;
