@@ -142,6 +142,7 @@ cudaError_t spmv_sweep(const merbit_plan_s* p, merbit_dtype vdt, const void* val
                        const float* x, const SweepParams& prm, cudaStream_t st);
 
 // Largest grid worth launching for a kernel (SMs x resident CTAs), cached.
-int persistent_grid(const void* kernel, int threads, size_t smem, int num_sms);
+// smem_max: the largest dynamic shared memory any launch of this kernel may use.
+int persistent_grid(const void* kernel, int threads, size_t smem, size_t smem_max, int num_sms);
 
 }  // namespace merbit

@@ -165,17 +165,20 @@ cudaError_t build_dangling(merbit_plan_s* p, cudaStream_t st, unsigned long long
   return e;
 }
 
-int persistent_grid(const void* kernel, int threads, size_t smem, int num_sms) {
+int persistent_grid(const void* kernel, int threads, size_t smem, size_t smem_max, int num_sms) {
   static std::mutex mu;
-  static std::map<std::pair<const void*, size_t>, int> cache;
+  static std::map<const void*, size_t> attr;                     // dynamic smem limit set per kernel
+  static std::map<std::pair<const void*, size_t>, int> cache;    // resident CTAs per SM
   std::lock_guard<std::mutex> lock(mu);
   auto key = std::make_pair(kernel, smem);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second * num_sms;
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  // the limit is raised once to the largest size any plan of this kernel needs, never lowered
+  if (smem_max > 48 * 1024 && attr[kernel] < smem_max) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) !=
         cudaSuccess)
       return 0;
+    attr[kernel] = smem_max;
   }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)

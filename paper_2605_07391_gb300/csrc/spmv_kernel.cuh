@@ -693,7 +693,9 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   if (p->nb == 0) return cudaSuccess;
   auto kern = merbit_spmv_kernel<VT, XT, AT, Epi>;
   const size_t smem = kStages * stage_bytes<VT>(p->sigma);
-  int grid = persistent_grid(reinterpret_cast<const void*>(kern), kThreads, smem, p->num_sms);
+  const size_t smem_max = kStages * stage_bytes<VT>(kSigmaMax);
+  int grid = persistent_grid(reinterpret_cast<const void*>(kern), kThreads, smem, smem_max,
+                             p->num_sms);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   if ((int64_t)grid > p->nb) grid = (int)p->nb;
   if (grid > kMaxParts) grid = kMaxParts;
