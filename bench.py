@@ -222,7 +222,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work (cpu_baseline)")
     ap.add_argument("--no-pagerank", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
-    ap.add_argument("--inner-sweeps", type=int, default=16)
+    ap.add_argument("--inner-sweeps", type=int, default=32, help="max inner sweeps per refinement step")
+    ap.add_argument("--sigma", type=int, default=14, help="steps per lane of the plan")
     args = ap.parse_args()
     rank, world, local = dist_setup()
     if args.impl == "reference":
@@ -259,7 +260,7 @@ def main():
     torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    p = mb.plan(row_ptr, col, stream=stream)
+    p = mb.plan(row_ptr, col, sigma=args.sigma, stream=stream)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     plan_ms = ev0.elapsed_time(ev1)

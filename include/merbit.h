@@ -185,20 +185,24 @@ merbit_status merbit_pagerank(merbit_plan_t plan, merbit_dtype dtype, const void
  *                pi F64.  Each step computes r = b - M pi in FP64
  *                (M = I - alpha P^T - (alpha/n) 1 d^T, b = (1-alpha)/n 1), stops
  *                when ||r||_1 < tol, then solves M delta = r approximately by
- *                1 + inner_sweeps Richardson sweeps with reduced-precision
- *                values, f32 vectors, f32 accumulation and FP64 dangling sums,
- *                and sets pi += delta (FP64).
- *   inner_sweeps IR modes: SpMV sweeps per refinement step (>= 1).
+ *                Richardson sweeps delta <- alpha P~^T delta + (alpha/n)(d^T delta) + r
+ *                from delta = r, with reduced-precision values P~, f32 vectors,
+ *                f32 accumulation and FP64 dangling sums, and sets pi += delta
+ *                (FP64).
+ *   inner_sweeps IR modes: maximum sweeps per refinement step (>= 1).
+ *   inner_tol    IR modes: the sweeps of a step stop once one sweep changes
+ *                delta by less than inner_tol * ||r||_1 (L1); 0 selects the unit
+ *                roundoff of the inner values (2^-8 bf16, 2^-11 f16, 2^-20 for f32).
  *   iters_out    host, may be NULL: updates (PLAIN) or refinement steps (IR).
  *   resid_out    host, may be NULL: the last L1 residual computed.
- *   resid_hist   host, may be NULL, max_iter entries: residual per update /
- *                per refinement step.
+ *   resid_hist   host, may be NULL: residual per update (PLAIN, max_iter
+ *                entries) or per residual evaluation (IR, max_iter + 1 entries).
  * Synchronises `stream`.
  */
 merbit_status merbit_pagerank_ex(merbit_plan_t plan, merbit_dtype dtype, const void* vals,
                                  double alpha, double tol, int max_iter, merbit_precision mode,
-                                 int inner_sweeps, void* pi, int* iters_out, double* resid_out,
-                                 double* resid_hist, void* stream);
+                                 int inner_sweeps, double inner_tol, void* pi, int* iters_out,
+                                 double* resid_out, double* resid_hist, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* merbit_last_error(void);

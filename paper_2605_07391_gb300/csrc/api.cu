@@ -541,12 +541,18 @@ merbit_status pagerank_plain(merbit_plan_s* p, const T* vals, double alpha, doub
 }
 
 merbit_status pagerank_ir(merbit_plan_s* p, const double* vals, double alpha, double tol,
-                          int max_steps, merbit_precision mode, int sweeps, double* pi,
-                          int* iters_out, double* resid_out, double* resid_hist,
+                          int max_steps, merbit_precision mode, int max_sweeps, double inner_tol,
+                          double* pi, int* iters_out, double* resid_out, double* resid_hist,
                           cudaStream_t st) {
   const int64_t n = p->n_rows;
   const merbit_dtype ldt = mode == MERBIT_IR_BF16 ? MERBIT_BF16
                            : mode == MERBIT_IR_F16 ? MERBIT_F16 : MERBIT_F32;
+  // inner stop: a sweep smaller than eta * ||r||_1 is below the rounding level of the
+  // reduced-precision values (unit roundoff 2^-8, 2^-11, 2^-24), so further sweeps
+  // cannot improve the correction
+  const double eta = inner_tol > 0.0 ? inner_tol
+                     : ldt == MERBIT_BF16 ? std::ldexp(1.0, -8)
+                     : ldt == MERBIT_F16 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -20);
   const size_t lo_bytes = align256(dtype_size(ldt) * (size_t)std::max<int64_t>(p->nnz, 1));
   const size_t vb = align256(sizeof(float) * (size_t)n);
   MB_TRY(grow(&p->scratch, &p->scratch_bytes, lo_bytes + 3 * vb));
@@ -559,7 +565,7 @@ merbit_status pagerank_ir(merbit_plan_s* p, const double* vals, double alpha, do
   if (merbit_status s = convert_typed(vals, lo, ldt, p->nnz, ldt == MERBIT_F16, &scale_exp, st,
                                       p->num_sms))
     return s;
-  const size_t per_step = (size_t)sweeps + 1;
+  const size_t per_step = (size_t)max_sweeps + 2;
   if (merbit_status s = ensure_hist(p, ((size_t)max_steps + 1) * per_step + 1)) return s;
   const double d0 = (double)p->n_dangling / (double)n;
   fill_kernel<double><<<grid_for(n, p->num_sms), 256, 0, st>>>(pi, n, 1.0 / (double)n);
@@ -571,7 +577,7 @@ merbit_status pagerank_ir(merbit_plan_s* p, const double* vals, double alpha, do
   StateWord w{};
   int step = 0;
   for (; step <= max_steps; ++step) {
-    // r = b - M pi  (FP64), stops the solve when ||r||_1 < tol
+    // r = b - M pi  (FP64); the solve stops once ||r||_1 < tol
     ResidParams rp;
     rp.rhs = rhs;
     rp.dang = p->dangling_bits;
@@ -581,12 +587,15 @@ merbit_status pagerank_ir(merbit_plan_s* p, const double* vals, double alpha, do
     rp.d_in = p->hist + 2 * L + 1;
     rp.s_out = p->hist + 2 * (L + 1);
     rp.iter = step;
+    const double* rnorm = rp.s_out;
     resid_launch.push_back(L);
     cudaError_t e = spmv_resid_f64(p, vals, pi, rp, st);
     if (e != cudaSuccess) return cuda_fail(e, "residual launch");
     ++L;
     if (step >= max_steps) break;   // final residual of the last correction
-    for (int s = 1; s <= sweeps; ++s) {
+    // inner Richardson sweeps on M delta = r, from delta = r; launches after the
+    // inner stop fired return at once
+    for (int s = 1; s <= max_sweeps; ++s) {
       SweepParams sp;
       sp.out = dl[(s + 1) & 1];
       sp.rhs = rhs;
@@ -596,13 +605,17 @@ merbit_status pagerank_ir(merbit_plan_s* p, const double* vals, double alpha, do
       sp.scale = scale;
       sp.d_in = p->hist + 2 * L + 1;
       sp.s_out = p->hist + 2 * (L + 1);
-      sp.pi64 = pi;
-      sp.last = s == sweeps;
+      sp.rnorm = rnorm;
+      sp.eta = eta;
       const float* xin = s == 1 ? rhs : dl[s & 1];
       e = spmv_sweep(p, ldt, lo, xin, sp, st);
       if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
       ++L;
     }
+    // pi += delta
+    e = ir_apply(p, pi, p->hist + 2 * (L + 1), st);
+    if (e != cudaSuccess) return cuda_fail(e, "apply launch");
+    ++L;
     MB_TRY(read_state(p, st, &w));
     if (w.err || w.done) break;
   }
@@ -636,8 +649,8 @@ extern "C" {
 
 merbit_status merbit_pagerank_ex(merbit_plan_t p, merbit_dtype dtype, const void* vals,
                                  double alpha, double tol, int max_iter, merbit_precision mode,
-                                 int inner_sweeps, void* pi, int* iters_out, double* resid_out,
-                                 double* resid_hist, void* stream) {
+                                 int inner_sweeps, double inner_tol, void* pi, int* iters_out,
+                                 double* resid_out, double* resid_hist, void* stream) {
   if (merbit_status s = check_plan(p)) return s;
   if (p->n_rows != p->n_cols) return fail(MERBIT_EINVAL, "PageRank needs a square plan");
   if (!(alpha >= 0.0 && alpha < 1.0)) return fail(MERBIT_EINVAL, "alpha must be in [0, 1)");
@@ -665,13 +678,14 @@ merbit_status merbit_pagerank_ex(merbit_plan_t p, merbit_dtype dtype, const void
     return fail(MERBIT_EINVAL, "unknown precision mode %d", (int)mode);
   if (dtype != MERBIT_F64) return fail(MERBIT_EINVAL, "refinement modes need F64 master values and pi");
   if (inner_sweeps < 1) return fail(MERBIT_EINVAL, "inner_sweeps must be >= 1");
+  if (inner_tol < 0.0) return fail(MERBIT_EINVAL, "inner_tol must be >= 0");
   return pagerank_ir(p, static_cast<const double*>(vals), alpha, tol, max_iter, mode, inner_sweeps,
-                     static_cast<double*>(pi), iters_out, resid_out, resid_hist, st);
+                     inner_tol, static_cast<double*>(pi), iters_out, resid_out, resid_hist, st);
 }
 
 merbit_status merbit_pagerank(merbit_plan_t p, merbit_dtype dtype, const void* vals, double alpha,
                               double tol, void* pi) {
-  return merbit_pagerank_ex(p, dtype, vals, alpha, tol, 10000, MERBIT_PLAIN, 0, pi, nullptr,
+  return merbit_pagerank_ex(p, dtype, vals, alpha, tol, 10000, MERBIT_PLAIN, 0, 0.0, pi, nullptr,
                             nullptr, nullptr, nullptr);
 }
 

@@ -26,6 +26,9 @@ struct RedState {
   int err;        // bit 0: an mbarrier wait expired
   int done;       // PageRank: a fused launch found its residual below tol
   int iters;      // number of launches counted when `done` was set
+  int inner_done; // refinement: the inner sweeps of the current step have converged
+  int pad_;
+  const float* delta;   // refinement: buffer holding the latest inner iterate
 };
 
 struct Geometry {
@@ -114,15 +117,15 @@ struct ResidParams {
 
 // Mixed-precision refinement: one inner Richardson sweep.
 struct SweepParams {
-  float* out;                   // next inner iterate (unused when last)
+  float* out;                   // next inner iterate
   const float* rhs;
   const uint32_t* dang;
   double alpha, inv_n;
   float scale;                  // 2^-scale_exp of pre-scaled values
   const double* d_in;           // dangling sum of the current inner iterate
-  double* s_out;                // [0] = L1 step size, [1] = dangling sum (of pi when last)
-  double* pi64;                 // updated in place when last
-  int last;
+  double* s_out;                // [0] = L1 size of this sweep, [1] = dangling sum of `out`
+  const double* rnorm;          // ||r||_1 of the current refinement step
+  double eta;                   // inner stop: sweep size <= eta * ||r||_1
 };
 
 // ---- launchers (one translation unit per value type) ----
@@ -140,6 +143,8 @@ cudaError_t spmv_resid_f64(const merbit_plan_s* p, const double* vals, const dou
                            const ResidParams& prm, cudaStream_t st);
 cudaError_t spmv_sweep(const merbit_plan_s* p, merbit_dtype vdt, const void* vals,
                        const float* x, const SweepParams& prm, cudaStream_t st);
+// pi += delta (FP64) with delta = the refinement's latest inner iterate; s_out[1] = dangling mass
+cudaError_t ir_apply(const merbit_plan_s* p, double* pi, double* s_out, cudaStream_t st);
 
 // Largest grid worth launching for a kernel (SMs x resident CTAs), cached.
 // smem_max: the largest dynamic shared memory any launch of this kernel may use.

@@ -106,6 +106,12 @@ __device__ __forceinline__ double ld_x(const double* p, uint64_t pol) {
   return v;
 }
 
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 __device__ __forceinline__ float widen(float v) { return v; }
 __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -211,6 +217,8 @@ struct EpiResid {
   __device__ __forceinline__ void finish(double A, double B, RedState* red) const {
     p.s_out[0] = A;
     p.s_out[1] = B;
+    red->delta = p.rhs;           // the first inner iterate is r itself
+    red->inner_done = 0;
     if (A < p.tol) {
       red->iters = p.iter + 1;
       red->done = 1;
@@ -218,7 +226,7 @@ struct EpiResid {
   }
 };
 
-// delta'[r] = alpha 2^-k (P~^T delta)[r] + (alpha/n) D_delta + rhs[r]; last sweep: pi += delta'
+// delta'[r] = alpha 2^-k (P~^T delta)[r] + (alpha/n) D_delta + rhs[r]
 struct EpiSweep {
   static constexpr bool kReduce = true;
   SweepParams p;
@@ -229,19 +237,13 @@ struct EpiSweep {
     c = static_cast<float>(p.alpha * p.inv_n * (*p.d_in));
   }
   __device__ __forceinline__ bool skip(const RedState* red) const {
-    return *reinterpret_cast<const volatile int*>(&red->done) != 0;
+    return *reinterpret_cast<const volatile int*>(&red->done) != 0 ||
+           *reinterpret_cast<const volatile int*>(&red->inner_done) != 0;
   }
   __device__ __forceinline__ void put(int r, float d, double& p0, double& p1) const {
-    if (!p.last) {
-      p.out[r] = d;
-      p0 += fabs(static_cast<double>(d) - static_cast<double>(xin[r]));
-      if (is_dangling(p.dang, r)) p1 += static_cast<double>(d);
-    } else {
-      const double v = p.pi64[r] + static_cast<double>(d);
-      p.pi64[r] = v;
-      p0 += fabs(static_cast<double>(d));
-      if (is_dangling(p.dang, r)) p1 += v;
-    }
+    p.out[r] = d;
+    p0 += fabs(static_cast<double>(d) - static_cast<double>(xin[r]));
+    if (is_dangling(p.dang, r)) p1 += static_cast<double>(d);
   }
   __device__ __forceinline__ void row(int r, float s, double& p0, double& p1) const {
     put(r, as * s + (c + p.rhs[r]), p0, p1);
@@ -249,9 +251,11 @@ struct EpiSweep {
   __device__ __forceinline__ void row64(int r, double s, double& p0, double& p1) const {
     put(r, static_cast<float>(static_cast<double>(as) * s) + (c + p.rhs[r]), p0, p1);
   }
-  __device__ __forceinline__ void finish(double A, double B, RedState*) const {
+  __device__ __forceinline__ void finish(double A, double B, RedState* red) const {
     p.s_out[0] = A;
     p.s_out[1] = B;
+    red->delta = p.out;
+    if (A <= p.eta * (*p.rnorm)) red->inner_done = 1;
   }
 };
 
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       m.txe = __ldg(g.tile_x + ti + 1);
       m.tys = __ldg(g.tile_y + ti);
       const int j = ti * kOmega + lane;
-      if (!(m.tys & kMsb) && j < g.lane_num) m.desc = __ldg(g.lane_desc + j);
+      if (!(m.tys & kMsb) && j < g.lane_num) m.desc = ld_stream(g.lane_desc + j, pol_stream);
     }
     return m;
   };
@@ -543,26 +547,26 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint32_t valid = (1u << lane_len) - 1u;
         const uint32_t dm = (cur.desc >> 18) & valid;     // down steps
         const uint32_t rm = ~(cur.desc >> 18) & valid;    // right steps
-        int xo = (int)(cur.desc & 511u);
-        int yo = active ? (int)((cur.desc >> 9) & 511u) : (g.n_rows - y_ws);
+        const int y0 = active ? (int)((cur.desc >> 9) & 511u) : (g.n_rows - y_ws);
+        const AT* pl = pt + (int)(cur.desc & 511u);   // this lane's first product
         AT sum = AT(0);
-        bool first = true;
 #pragma unroll
         for (int k = 0; k < kSigmaMax; ++k) {
-          const uint32_t d = (dm >> k) & 1u;
-          const uint32_t rr = (rm >> k) & 1u;
-          const AT pv = pt[xo];
-          if (d) {
-            // down step: the row in progress ends inside this lane; it may have
-            // begun in earlier lanes only if this is the lane's first down step
-            if (first) atomicAdd(sy + yo, sum);
-            else sy[yo] = sum;
-            first = false;
+          // step k consumes product k - (down steps before k); the address depends on
+          // the descriptor only, so every load can be issued ahead of the additions
+          const int nd = __popc(dm & ((1u << k) - 1u));
+          const AT pv = pl[k - nd];
+          if ((dm >> k) & 1u) {
+            // down step: row y0 + nd ends here; only the lane's first such row can
+            // have begun in an earlier lane, so only that one needs an atomic add
+            if (nd == 0) atomicAdd(sy + y0, sum);
+            else sy[y0 + nd] = sum;
+            sum = AT(0);
+          } else if ((rm >> k) & 1u) {
+            sum += pv;
           }
-          sum = d ? AT(0) : (rr ? sum + pv : sum);
-          xo += (int)rr;
-          yo += (int)d;
         }
+        const int yo = y0 + __popc(dm);
         const bool head = lane == 0 || dm != 0u;
         // segmented inclusive scan of trailing sums; heads start segments
         AT sv_ = sum;
@@ -625,6 +629,43 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
+// Grid-wide FP64 sums of (p0, p1) over a launch of blockDim.x <= 256 threads:
+// block sums go to spread slots, and the last CTA to arrive adds the slots in a
+// fixed order, clears them and calls finish(A, B).
+template <typename F>
+__device__ __forceinline__ void grid_sum2(double p0, double p1, RedState* red, F finish) {
+  __shared__ double red_smem[8][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  p0 = warp_sum(p0);
+  p1 = warp_sum(p1);
+  if (lane == 0) {
+    red_smem[warp][0] = p0;
+    red_smem[warp][1] = p1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      a += red_smem[w][0];
+      b += red_smem[w][1];
+    }
+    const int q = blockIdx.x % kRedSlots;
+    atomicAdd(&red->slot[q][0], a);
+    atomicAdd(&red->slot[q][1], b);
+    __threadfence();
+    if (atomicAdd(&red->arrive, 1u) + 1 == gridDim.x) {
+      __threadfence();
+      double A = 0.0, B = 0.0;
+      for (int i = 0; i < kRedSlots; ++i) {
+        A += read_reset(&red->slot[i][0]);
+        B += read_reset(&red->slot[i][1]);
+      }
+      red->arrive = 0u;
+      finish(A, B);
+    }
+  }
+}
+
 // Second pass: rows shared between blocks (one thread per distinct boundary
 // row: the FP64 total of its accumulator goes through the epilogue, and the
 // accumulator is cleared), then the grid-wide FP64 reductions: per-CTA
@@ -632,8 +673,6 @@ __global__ void __launch_bounds__(kThreads, 2)
 template <typename Epi>
 __global__ void __launch_bounds__(256) merbit_finalize_kernel(const Geometry g, Epi epi,
                                                               int nparts) {
-  __shared__ double red_smem[8][2];
-  __shared__ bool last;
   if (epi.skip(g.red)) return;
   epi.init();
   double p0 = 0.0, p1 = 0.0;
@@ -653,37 +692,7 @@ __global__ void __launch_bounds__(256) merbit_finalize_kernel(const Geometry g, 
       p0 += q.x;
       p1 += q.y;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    p0 = warp_sum(p0);
-    p1 = warp_sum(p1);
-    if (lane == 0) {
-      red_smem[warp][0] = p0;
-      red_smem[warp][1] = p1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
-        a += red_smem[w][0];
-        b += red_smem[w][1];
-      }
-      RedState* red = g.red;
-      const int q = blockIdx.x % kRedSlots;
-      atomicAdd(&red->slot[q][0], a);
-      atomicAdd(&red->slot[q][1], b);
-      __threadfence();
-      last = atomicAdd(&red->arrive, 1u) + 1 == gridDim.x;
-      if (last) {
-        __threadfence();
-        double A = 0.0, B = 0.0;
-        for (int i = 0; i < kRedSlots; ++i) {
-          A += read_reset(&red->slot[i][0]);
-          B += read_reset(&red->slot[i][1]);
-        }
-        red->arrive = 0u;
-        epi.finish(A, B, red);
-      }
-    }
+    grid_sum2(p0, p1, g.red, [&](double A, double B) { epi.finish(A, B, g.red); });
   }
 }
 

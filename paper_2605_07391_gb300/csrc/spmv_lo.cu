@@ -15,6 +15,35 @@ cudaError_t spmv_plain_lo(const merbit_plan_s* p, merbit_dtype vdt, const void* 
   return cudaErrorInvalidValue;
 }
 
+// pi += delta in FP64, delta the refinement's latest inner iterate (recorded on
+// the device by the residual / sweep launches); s_out = (||delta||_1, dangling mass of pi).
+__global__ void __launch_bounds__(256) ir_apply_kernel(double* __restrict__ pi, int n,
+                                                       const uint32_t* __restrict__ dang,
+                                                       RedState* red, double* s_out) {
+  if (*reinterpret_cast<const volatile int*>(&red->done)) return;
+  const float* delta = *reinterpret_cast<const float* const volatile*>(&red->delta);
+  double p0 = 0.0, p1 = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double d = static_cast<double>(delta[i]);
+    const double v = pi[i] + d;
+    pi[i] = v;
+    p0 += fabs(d);
+    if (is_dangling(dang, i)) p1 += v;
+  }
+  grid_sum2(p0, p1, red, [&](double A, double B) {
+    s_out[0] = A;
+    s_out[1] = B;
+    red->inner_done = 0;
+  });
+}
+
+cudaError_t ir_apply(const merbit_plan_s* p, double* pi, double* s_out, cudaStream_t st) {
+  const int n = (int)p->n_rows;
+  const int grid = std::max(1, std::min((n + 255) / 256, p->num_sms * 8));
+  ir_apply_kernel<<<grid, 256, 0, st>>>(pi, n, p->dangling_bits, p->red, s_out);
+  return cudaGetLastError();
+}
+
 cudaError_t spmv_sweep(const merbit_plan_s* p, merbit_dtype vdt, const void* vals,
                        const float* x, const SweepParams& prm, cudaStream_t st) {
   EpiSweep epi{};

@@ -76,7 +76,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_spmv_host": [vp, i32, vp, vp, vp, vp],
             "merbit_vals_convert": [vp, i32, vp, i32, i64, i32, ctypes.POINTER(i32), vp],
             "merbit_pagerank": [vp, i32, vp, dbl, dbl, vp],
-            "merbit_pagerank_ex": [vp, i32, vp, dbl, dbl, i32, i32, i32, vp,
+            "merbit_pagerank_ex": [vp, i32, vp, dbl, dbl, i32, i32, i32, dbl, vp,
                                    ctypes.POINTER(i32), ctypes.POINTER(dbl), vp, vp],
         }
         for name, args in sig.items():
@@ -236,8 +236,9 @@ def vals_convert(src: torch.Tensor, dtype: torch.dtype, auto_scale: bool = False
 
 
 def pagerank(p: Plan, vals: torch.Tensor, alpha: float = 0.85, tol: float = 1e-10,
-             max_iter: int = 10000, mode: str = "plain", inner_sweeps: int = 16,
-             pi: torch.Tensor | None = None, stream=None, history: bool = False) -> tuple[torch.Tensor, dict]:
+             max_iter: int = 10000, mode: str = "plain", inner_sweeps: int = 32,
+             inner_tol: float = 0.0, pi: torch.Tensor | None = None, stream=None,
+             history: bool = False) -> tuple[torch.Tensor, dict]:
     """merbit_pagerank_ex.  Returns (pi, info) with info keys iters, resid, converged[, hist]."""
     _need_cuda(vals, pi)
     m = MODES[mode]
@@ -248,7 +249,7 @@ def pagerank(p: Plan, vals: torch.Tensor, alpha: float = 0.85, tol: float = 1e-1
     resid = ctypes.c_double(0.0)
     hist = np.zeros(max_iter + 1, np.float64) if history else None
     st = _check("merbit_pagerank_ex", load().merbit_pagerank_ex(
-        p.handle, _dt(vals), _ptr(vals), alpha, tol, max_iter, m, inner_sweeps, _ptr(pi),
+        p.handle, _dt(vals), _ptr(vals), alpha, tol, max_iter, m, inner_sweeps, inner_tol, _ptr(pi),
         ctypes.byref(iters), ctypes.byref(resid),
         ctypes.c_void_p(hist.ctypes.data) if history else ctypes.c_void_p(0), _stream(stream)),
         allow=(5,))

@@ -207,3 +207,12 @@ def test_spmv_full_config2(cuda_device, variant):
         # rows with no entries are exactly zero
         empty = np.diff(a.row_ptr) == 0
         assert np.count_nonzero(as_f64(y)[empty]) == 0
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_spmv_plans_of_different_sigma_interleaved(cuda_device, dtype):
+    """Plans with small and large sigma used alternately by the same kernel (the larger
+    stage size must stay launchable after a smaller one)."""
+    a = inputs.rmat_uniform(13, 16, 5, 5)
+    for sigma in (7, 14, 1, 14, 7):
+        _run(a, dtype, sigma=sigma)
