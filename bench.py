@@ -374,7 +374,8 @@ def main():
                 torch.cuda.synchronize(dev)
                 ms = (time.perf_counter() - t0) * 1e3
                 rec = {"ms": ms, "iters": info["iters"], "resid": info["resid"],
-                       "converged": info["converged"], "end_to_end_ms": ms + plan_ms}
+                       "converged": info["converged"], "end_to_end_ms": ms + plan_ms,
+                       "spmv_launches": info["spmv_launches"]}
                 if mode != "plain":
                     rec["inner_sweeps"] = args.inner_sweeps
                 if not args.no_oracle_check:

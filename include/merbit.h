@@ -192,17 +192,20 @@ merbit_status merbit_pagerank(merbit_plan_t plan, merbit_dtype dtype, const void
  *   inner_sweeps IR modes: maximum sweeps per refinement step (>= 1).
  *   inner_tol    IR modes: the sweeps of a step stop once one sweep changes
  *                delta by less than inner_tol * ||r||_1 (L1); 0 selects the unit
- *                roundoff of the inner values (2^-8 bf16, 2^-11 f16, 2^-20 for f32).
+ *                roundoff of the inner values (2^-8 bf16, 2^-11 f16) and 2^-17 for f32.
  *   iters_out    host, may be NULL: updates (PLAIN) or refinement steps (IR).
  *   resid_out    host, may be NULL: the last L1 residual computed.
  *   resid_hist   host, may be NULL: residual per update (PLAIN, max_iter
  *                entries) or per residual evaluation (IR, max_iter + 1 entries).
+ *   launches_out host, may be NULL: SpMV launches that did work (PLAIN: the
+ *                updates; IR: residual evaluations plus inner sweeps).
  * Synchronises `stream`.
  */
 merbit_status merbit_pagerank_ex(merbit_plan_t plan, merbit_dtype dtype, const void* vals,
                                  double alpha, double tol, int max_iter, merbit_precision mode,
                                  int inner_sweeps, double inner_tol, void* pi, int* iters_out,
-                                 double* resid_out, double* resid_hist, void* stream);
+                                 double* resid_out, double* resid_hist, int* launches_out,
+                                 void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* merbit_last_error(void);

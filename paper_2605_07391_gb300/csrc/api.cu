@@ -89,7 +89,7 @@ cudaError_t reset_device_state(merbit_plan_s* p, cudaStream_t st) {
 }
 
 // err, done, iters of the plan's RedState, read through pinned memory.
-struct StateWord { int err, done, iters; };
+struct StateWord { int err, done, iters, inner_done, launches; };
 
 cudaError_t read_state(merbit_plan_s* p, cudaStream_t st, StateWord* w) {
   cudaError_t e = cudaMemcpyAsync(p->host_pinned, &p->red->err, sizeof(StateWord),
@@ -119,6 +119,8 @@ __global__ void pr_state_init_kernel(double* hist, double d0, RedState* red) {
   hist[1] = d0;
   red->done = 0;
   red->iters = 0;
+  red->inner_done = 0;
+  red->launches = 0;
 }
 
 // Correctly rounded (ties to even) float64 -> IEEE binary format with E
@@ -486,7 +488,7 @@ namespace {
 template <typename T>
 merbit_status pagerank_plain(merbit_plan_s* p, const T* vals, double alpha, double tol,
                              int max_iter, T* pi, int* iters_out, double* resid_out,
-                             double* resid_hist, cudaStream_t st) {
+                             double* resid_hist, int* launches_out, cudaStream_t st) {
   const int64_t n = p->n_rows;
   MB_TRY(grow(&p->scratch, &p->scratch_bytes, align256(sizeof(T) * (size_t)n)));
   if (merbit_status s = ensure_hist(p, (size_t)max_iter)) return s;
@@ -531,6 +533,7 @@ merbit_status pagerank_plain(merbit_plan_s* p, const T* vals, double alpha, doub
   MB_TRY(cudaMemcpyAsync(h.data(), p->hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   MB_TRY(cudaStreamSynchronize(st));
   if (iters_out) *iters_out = iters;
+  if (launches_out) *launches_out = iters;
   if (resid_out) *resid_out = iters > 0 ? h[2 * (size_t)iters] : 0.0;
   if (resid_hist)
     for (int i = 0; i < iters; ++i) resid_hist[i] = h[2 * ((size_t)i + 1)];
@@ -543,16 +546,17 @@ merbit_status pagerank_plain(merbit_plan_s* p, const T* vals, double alpha, doub
 merbit_status pagerank_ir(merbit_plan_s* p, const double* vals, double alpha, double tol,
                           int max_steps, merbit_precision mode, int max_sweeps, double inner_tol,
                           double* pi, int* iters_out, double* resid_out, double* resid_hist,
-                          cudaStream_t st) {
+                          int* launches_out, cudaStream_t st) {
   const int64_t n = p->n_rows;
   const merbit_dtype ldt = mode == MERBIT_IR_BF16 ? MERBIT_BF16
                            : mode == MERBIT_IR_F16 ? MERBIT_F16 : MERBIT_F32;
   // inner stop: a sweep smaller than eta * ||r||_1 is below the rounding level of the
-  // reduced-precision values (unit roundoff 2^-8, 2^-11, 2^-24), so further sweeps
-  // cannot improve the correction
+  // reduced-precision values (unit roundoff 2^-8 and 2^-11), so further sweeps cannot
+  // improve the correction; f32 values would allow far more, but a step gaining about
+  // five decades already balances sweeps against the FP64 residual evaluations
   const double eta = inner_tol > 0.0 ? inner_tol
                      : ldt == MERBIT_BF16 ? std::ldexp(1.0, -8)
-                     : ldt == MERBIT_F16 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -20);
+                     : ldt == MERBIT_F16 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -17);
   const size_t lo_bytes = align256(dtype_size(ldt) * (size_t)std::max<int64_t>(p->nnz, 1));
   const size_t vb = align256(sizeof(float) * (size_t)n);
   MB_TRY(grow(&p->scratch, &p->scratch_bytes, lo_bytes + 3 * vb));
@@ -633,6 +637,7 @@ merbit_status pagerank_ir(merbit_plan_s* p, const double* vals, double alpha, do
   const int corrections = w.done ? evals - 1 : std::min<int>(step, max_steps);
   const double last = h[2 * ((size_t)resid_launch[(size_t)evals - 1] + 1)];
   if (iters_out) *iters_out = corrections;
+  if (launches_out) *launches_out = w.launches;
   if (resid_out) *resid_out = last;
   if (resid_hist)
     for (int i = 0; i < evals; ++i)
@@ -650,7 +655,8 @@ extern "C" {
 merbit_status merbit_pagerank_ex(merbit_plan_t p, merbit_dtype dtype, const void* vals,
                                  double alpha, double tol, int max_iter, merbit_precision mode,
                                  int inner_sweeps, double inner_tol, void* pi, int* iters_out,
-                                 double* resid_out, double* resid_hist, void* stream) {
+                                 double* resid_out, double* resid_hist, int* launches_out,
+                                 void* stream) {
   if (merbit_status s = check_plan(p)) return s;
   if (p->n_rows != p->n_cols) return fail(MERBIT_EINVAL, "PageRank needs a square plan");
   if (!(alpha >= 0.0 && alpha < 1.0)) return fail(MERBIT_EINVAL, "alpha must be in [0, 1)");
@@ -668,10 +674,12 @@ merbit_status merbit_pagerank_ex(merbit_plan_t p, merbit_dtype dtype, const void
   if (mode == MERBIT_PLAIN) {
     if (dtype == MERBIT_F32)
       return pagerank_plain<float>(p, static_cast<const float*>(vals), alpha, tol, max_iter,
-                                   static_cast<float*>(pi), iters_out, resid_out, resid_hist, st);
+                                   static_cast<float*>(pi), iters_out, resid_out, resid_hist,
+                                   launches_out, st);
     if (dtype == MERBIT_F64)
       return pagerank_plain<double>(p, static_cast<const double*>(vals), alpha, tol, max_iter,
-                                    static_cast<double*>(pi), iters_out, resid_out, resid_hist, st);
+                                    static_cast<double*>(pi), iters_out, resid_out, resid_hist,
+                                    launches_out, st);
     return fail(MERBIT_EINVAL, "PLAIN PageRank: dtype must be F32 or F64");
   }
   if (mode != MERBIT_IR_BF16 && mode != MERBIT_IR_F16 && mode != MERBIT_IR_F32)
@@ -680,13 +688,14 @@ merbit_status merbit_pagerank_ex(merbit_plan_t p, merbit_dtype dtype, const void
   if (inner_sweeps < 1) return fail(MERBIT_EINVAL, "inner_sweeps must be >= 1");
   if (inner_tol < 0.0) return fail(MERBIT_EINVAL, "inner_tol must be >= 0");
   return pagerank_ir(p, static_cast<const double*>(vals), alpha, tol, max_iter, mode, inner_sweeps,
-                     inner_tol, static_cast<double*>(pi), iters_out, resid_out, resid_hist, st);
+                     inner_tol, static_cast<double*>(pi), iters_out, resid_out, resid_hist,
+                                    launches_out, st);
 }
 
 merbit_status merbit_pagerank(merbit_plan_t p, merbit_dtype dtype, const void* vals, double alpha,
                               double tol, void* pi) {
   return merbit_pagerank_ex(p, dtype, vals, alpha, tol, 10000, MERBIT_PLAIN, 0, 0.0, pi, nullptr,
-                            nullptr, nullptr, nullptr);
+                            nullptr, nullptr, nullptr, nullptr);
 }
 
 }  // extern "C"

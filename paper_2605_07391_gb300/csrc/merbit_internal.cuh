@@ -27,7 +27,7 @@ struct RedState {
   int done;       // PageRank: a fused launch found its residual below tol
   int iters;      // number of launches counted when `done` was set
   int inner_done; // refinement: the inner sweeps of the current step have converged
-  int pad_;
+  int launches;   // SpMV launches that did work since the solve started
   const float* delta;   // refinement: buffer holding the latest inner iterate
 };
 

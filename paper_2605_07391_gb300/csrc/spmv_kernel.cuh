@@ -185,6 +185,7 @@ struct EpiPageRank {
   __device__ __forceinline__ void finish(double A, double B, RedState* red) const {
     p.s_out[0] = A;
     p.s_out[1] = B;
+    ++red->launches;
     if (p.tol > 0.0 && A < p.tol) {
       red->iters = p.iter + 1;
       red->done = 1;
@@ -217,6 +218,7 @@ struct EpiResid {
   __device__ __forceinline__ void finish(double A, double B, RedState* red) const {
     p.s_out[0] = A;
     p.s_out[1] = B;
+    ++red->launches;
     red->delta = p.rhs;           // the first inner iterate is r itself
     red->inner_done = 0;
     if (A < p.tol) {
@@ -254,6 +256,7 @@ struct EpiSweep {
   __device__ __forceinline__ void finish(double A, double B, RedState* red) const {
     p.s_out[0] = A;
     p.s_out[1] = B;
+    ++red->launches;
     red->delta = p.out;
     if (A <= p.eta * (*p.rnorm)) red->inner_done = 1;
   }
@@ -549,13 +552,15 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint32_t rm = ~(cur.desc >> 18) & valid;    // right steps
         const int y0 = active ? (int)((cur.desc >> 9) & 511u) : (g.n_rows - y_ws);
         const AT* pl = pt + (int)(cur.desc & 511u);   // this lane's first product
+        // step k consumes product k - (down steps before k): the addresses depend on the
+        // descriptor only, so all loads are issued before any addition or flush
+        AT pv[kSigmaMax];
+#pragma unroll
+        for (int k = 0; k < kSigmaMax; ++k) pv[k] = pl[k - __popc(dm & ((1u << k) - 1u))];
         AT sum = AT(0);
 #pragma unroll
         for (int k = 0; k < kSigmaMax; ++k) {
-          // step k consumes product k - (down steps before k); the address depends on
-          // the descriptor only, so every load can be issued ahead of the additions
           const int nd = __popc(dm & ((1u << k) - 1u));
-          const AT pv = pl[k - nd];
           if ((dm >> k) & 1u) {
             // down step: row y0 + nd ends here; only the lane's first such row can
             // have begun in an earlier lane, so only that one needs an atomic add
@@ -563,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             else sy[y0 + nd] = sum;
             sum = AT(0);
           } else if ((rm >> k) & 1u) {
-            sum += pv;
+            sum += pv[k];
           }
         }
         const int yo = y0 + __popc(dm);

@@ -77,7 +77,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_vals_convert": [vp, i32, vp, i32, i64, i32, ctypes.POINTER(i32), vp],
             "merbit_pagerank": [vp, i32, vp, dbl, dbl, vp],
             "merbit_pagerank_ex": [vp, i32, vp, dbl, dbl, i32, i32, i32, dbl, vp,
-                                   ctypes.POINTER(i32), ctypes.POINTER(dbl), vp, vp],
+                                   ctypes.POINTER(i32), ctypes.POINTER(dbl), vp,
+                                   ctypes.POINTER(i32), vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -246,14 +247,16 @@ def pagerank(p: Plan, vals: torch.Tensor, alpha: float = 0.85, tol: float = 1e-1
     if pi is None:
         pi = torch.empty(p.n_rows, dtype=dtype, device=vals.device)
     iters = ctypes.c_int(0)
+    launches = ctypes.c_int(0)
     resid = ctypes.c_double(0.0)
     hist = np.zeros(max_iter + 1, np.float64) if history else None
     st = _check("merbit_pagerank_ex", load().merbit_pagerank_ex(
         p.handle, _dt(vals), _ptr(vals), alpha, tol, max_iter, m, inner_sweeps, inner_tol, _ptr(pi),
         ctypes.byref(iters), ctypes.byref(resid),
-        ctypes.c_void_p(hist.ctypes.data) if history else ctypes.c_void_p(0), _stream(stream)),
-        allow=(5,))
-    info = {"iters": iters.value, "resid": resid.value, "converged": st == 0}
+        ctypes.c_void_p(hist.ctypes.data) if history else ctypes.c_void_p(0),
+        ctypes.byref(launches), _stream(stream)), allow=(5,))
+    info = {"iters": iters.value, "resid": resid.value, "converged": st == 0,
+            "spmv_launches": launches.value}
     if history:
         n = iters.value if m == PLAIN else iters.value + 1
         info["hist"] = hist[:n].copy()
