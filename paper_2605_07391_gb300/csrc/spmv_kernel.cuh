@@ -263,302 +263,211 @@ struct EpiSweep {
 };
 
 // ---------------------------------------------------------------- kernel
-//
-// One persistent CTA per SM, three warp roles connected by mbarriers over a
-// ring of kStages shared-memory stages (each stage holds one block of tiles):
-//   producer warp (1)  : bulk copies of the block's values and column indices
-//                        (full[s] completes when both have landed);
-//   gather warps (4)   : one cp.async per nonzero, x[col[k]] -> xs[s][k]
-//                        (gathered[s] completes when every gather has landed);
-//   compute warps (8)  : one tile per warp: descriptor-driven lane scan over
-//                        vals[k] * xs[k], warp segmented sum, then the block
-//                        commit (empty[s] releases the stage to the producer).
-// The gathers of later blocks stay in flight while earlier blocks are reduced,
-// and no register holds a gathered value.
-
-constexpr int kComputeWarps = kTilesPerBlock;
-constexpr int kGatherWarps = 4;
-constexpr int kComputeThreads = kComputeWarps * 32;
-constexpr int kGatherThreads = kGatherWarps * 32;
-constexpr int kProducerWarp = kComputeWarps + kGatherWarps;
-constexpr int kCtaThreads = (kProducerWarp + 1) * 32;
-constexpr int kStagePad = 32;
 
 struct StageInfo {
   int x_bs, x_be, y_bs, y_be;   // block start / end coordinates
-  int a0, end;                  // values and column indices staged for [a0, end)
+  int a0v, endv;                // values staged for [a0v, endv)
+  int a0c, endc;                // column indices staged for [a0c, endc)
 };
 
-// Both bulk-copied arrays start at a multiple of A elements, so that values and
-// column indices start on 16-byte boundaries (bulk-copy rule).
 template <typename VT>
-__host__ __device__ constexpr int stage_align() {
-  return (16 / (int)sizeof(VT)) > 4 ? 16 / (int)sizeof(VT) : 4;
+__host__ __device__ constexpr int stage_cap(int sigma) {
+  return kThreads * sigma + 32;   // the lane scan may read up to 13 past the last product
 }
 
 __host__ __device__ inline size_t round128(size_t b) { return (b + 127) & ~size_t(127); }
 
-// Stage layout: vals[cap] | col[cap] | xs[cap] | s_y[cap], cap = 256*sigma + 32.
-template <typename VT, typename XT, typename AT>
-struct Layout {
-  size_t col_off, xs_off, sy_off, bytes;
-  __host__ __device__ explicit Layout(int sigma) {
-    const size_t cap = (size_t)kComputeThreads * sigma + kStagePad;
-    col_off = round128(cap * sizeof(VT));
-    xs_off = col_off + round128(cap * sizeof(int32_t));
-    sy_off = xs_off + round128(cap * sizeof(XT));
-    bytes = sy_off + round128(cap * sizeof(AT));
-  }
-};
-
-// As many stages (2 or 3) as fit in 200 KB at the largest sigma.
-template <typename VT, typename XT, typename AT>
-__host__ __device__ constexpr int stages_for() {
-  return 3 * ((size_t)kComputeThreads * kSigmaMax + kStagePad) *
-                     (sizeof(VT) + sizeof(int32_t) + sizeof(XT) + sizeof(AT)) + 3 * 512 <=
-                 200 * 1024
-             ? 3
-             : 2;
+template <typename VT>
+__host__ __device__ inline size_t stage_vals_bytes(int sigma) {
+  return round128(sizeof(VT) * (size_t)stage_cap<VT>(sigma));
+}
+template <typename VT>
+__host__ __device__ inline size_t stage_col_bytes(int sigma) {
+  return round128(sizeof(int32_t) * (size_t)stage_cap<VT>(sigma));
+}
+template <typename VT>
+__host__ __device__ inline size_t stage_bytes(int sigma) {
+  return stage_vals_bytes<VT>(sigma) + stage_col_bytes<VT>(sigma);
 }
 
-__device__ __forceinline__ void cp_async_gather(void* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_gather(void* dst, const double* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-// the mbarrier receives one arrival once all of this thread's earlier cp.async have landed
-__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-// barrier 1 among the compute warps only
-__device__ __forceinline__ void compute_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kComputeThreads) : "memory");
-}
-// barrier 1 among the compute warps, returning whether any of them passes true
-__device__ __forceinline__ bool compute_sync_or(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, %2, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "n"(kComputeThreads)
-      : "memory");
-  return r != 0;
-}
-
-// Per-warp tile metadata, loaded one block ahead.
-struct TileMeta {
-  uint32_t txs, txe, tys, desc;
+// Products go where an input of the same width was staged.
+template <typename VT, typename AT>
+struct ProdInVals {
+  static constexpr bool value = sizeof(VT) == sizeof(AT);
 };
 
 template <typename VT, typename XT, typename AT, typename Epi>
-__global__ void __launch_bounds__(kCtaThreads, 1)
+__global__ void __launch_bounds__(kThreads, 3)
     merbit_spmv_kernel(const Geometry g, const VT* __restrict__ vals, const XT* __restrict__ x,
                        Epi epi) {
-  constexpr int A = stage_align<VT>();
-  constexpr int S = stages_for<VT, XT, AT>();
-  __shared__ __align__(8) uint64_t full[S], gathered[S], empty[S];
-  __shared__ StageInfo info[S];
-  __shared__ double red_smem[kComputeWarps][2];
+  static_assert(ProdInVals<VT, AT>::value || sizeof(AT) == 4, "product slot width");
+  constexpr int VE = 16 / (int)sizeof(VT);   // values per 16 bytes
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ StageInfo info[2];
+  __shared__ double red_smem[kThreads / 32][2];
   extern __shared__ __align__(128) unsigned char dyn_smem[];
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
   const int G = gridDim.x;
-  const int v0 = blockIdx.x;
   if (epi.skip(g.red)) return;
+  epi.init();
 
-  const Layout<VT, XT, AT> L(g.sigma);
-  auto sv = [&](int s) { return reinterpret_cast<VT*>(dyn_smem + (size_t)s * L.bytes); };
-  auto sc = [&](int s) { return reinterpret_cast<int32_t*>(dyn_smem + (size_t)s * L.bytes + L.col_off); };
-  auto sx = [&](int s) { return reinterpret_cast<XT*>(dyn_smem + (size_t)s * L.bytes + L.xs_off); };
-  auto sy = [&](int s) { return reinterpret_cast<AT*>(dyn_smem + (size_t)s * L.bytes + L.sy_off); };
-  // block b of this CTA is v0 + b*G, in stage b % S for the (b / S)-th time
-  auto nblocks = [&]() { return v0 < g.nb ? (g.nb - 1 - v0) / G + 1 : 0; };
-  const int nbk = nblocks();
+  const size_t svb = stage_vals_bytes<VT>(g.sigma);
+  const size_t stb = stage_bytes<VT>(g.sigma);
+  auto sv = [&](int s) { return reinterpret_cast<VT*>(dyn_smem + (size_t)s * stb); };
+  auto sc = [&](int s) { return reinterpret_cast<int32_t*>(dyn_smem + (size_t)s * stb + svb); };
+
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_x = policy_evict_last();
+  const int nnz_v = g.nnz & ~(VE - 1);
+  const int nnz_c = g.nnz & ~3;
+
+  // geometry of block v, as needed to issue its copies (thread 0 only)
+  auto geom_of = [&](int v, int& xb, int& xe, uint32_t& yb, uint32_t& ye) {
+    const int bs = v * kTilesPerBlock;
+    const int be = min(bs + kTilesPerBlock, g.tile_num);
+    xb = (int)g.tile_x[bs];
+    xe = (int)g.tile_x[be];
+    yb = g.tile_y[bs] & ~kMsb;
+    ye = g.tile_y[be] & ~kMsb;
+  };
+  auto issue = [&](int s, int xb, int xe, uint32_t yb, uint32_t ye) {
+    StageInfo in;
+    in.x_bs = xb; in.x_be = xe; in.y_bs = (int)yb; in.y_be = (int)ye;
+    in.a0v = xb & ~(VE - 1);
+    in.endv = max(in.a0v, min((xe + VE - 1) & ~(VE - 1), nnz_v));
+    in.a0c = xb & ~3;
+    in.endc = max(in.a0c, min((xe + 3) & ~3, nnz_c));
+    info[s] = in;
+    const uint32_t bv = (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT);
+    const uint32_t bc = (uint32_t)(in.endc - in.a0c) * 4u;
+    mbar_arrive_expect_tx(&mbar[s], bv + bc);
+    if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, &mbar[s], pol_stream);
+    if (bc) bulk_g2s(sc(s), g.col + in.a0c, bc, &mbar[s], pol_stream);
+  };
 
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&gathered[s], kGatherThreads);
-      mbar_init(&empty[s], kComputeThreads);
-    }
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
     fence_mbar_init();
   }
   __syncthreads();
-
-  if (warp == kProducerWarp) {
-    // ------------------------------------------------------------ producer
-    if (lane != 0) return;
-    const uint64_t pol_stream = policy_evict_first();
-    const int nnz_a = g.nnz & ~(A - 1);
-    int b = 0;
-    bool ok = true;
-    for (; b < nbk; ++b) {
-      const int s = b % S;
-      if (b >= S && !mbar_wait_bounded(&empty[s], (uint32_t)((b / S - 1) & 1))) {
-        atomicOr(&g.red->err, 1);
-        ok = false;
-        break;
-      }
-      const int v = v0 + b * G;
-      const int bs = v * kTilesPerBlock;
-      const int be = min(bs + kTilesPerBlock, g.tile_num);
-      StageInfo in;
-      in.x_bs = (int)g.tile_x[bs];
-      in.x_be = (int)g.tile_x[be];
-      in.y_bs = (int)(g.tile_y[bs] & ~kMsb);
-      in.y_be = (int)(g.tile_y[be] & ~kMsb);
-      in.a0 = in.x_bs & ~(A - 1);
-      in.end = max(in.a0, min((in.x_be + A - 1) & ~(A - 1), nnz_a));
-      info[s] = in;
-      const uint32_t cnt = (uint32_t)(in.end - in.a0);
-      mbar_arrive_expect_tx(&full[s], cnt * (uint32_t)(sizeof(VT) + sizeof(int32_t)));
-      if (cnt) {
-        bulk_g2s(sv(s), vals + in.a0, cnt * (uint32_t)sizeof(VT), &full[s], pol_stream);
-        bulk_g2s(sc(s), g.col + in.a0, cnt * 4u, &full[s], pol_stream);
-      }
-    }
-    if (!ok) {
-      // let the copies already issued land before this CTA can retire
-      for (int q = max(0, b - S); q < b; ++q) mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1));
-    }
-    return;
+  if (tid == 0) {
+    int xb, xe; uint32_t yb, ye;
+    if (blockIdx.x < g.nb) { geom_of(blockIdx.x, xb, xe, yb, ye); issue(0, xb, xe, yb, ye); }
+    if (blockIdx.x + G < g.nb) { geom_of(blockIdx.x + G, xb, xe, yb, ye); issue(1, xb, xe, yb, ye); }
   }
 
-  if (warp >= kComputeWarps) {
-    // ------------------------------------------------------------ gather warps
-    const int gt = tid - kComputeThreads;
-    const uint64_t pol_x = policy_evict_last();
-    (void)pol_x;
-    for (int b = 0; b < nbk; ++b) {
-      const int s = b % S;
-      if (!mbar_wait_bounded(&full[s], (uint32_t)((b / S) & 1))) {
-        atomicOr(&g.red->err, 1);
-        break;
-      }
-      const StageInfo in = info[s];
-      const int32_t* col_s = sc(s);
-      XT* xs = sx(s);
-      const int e0 = in.x_bs - in.a0, e1 = in.x_be - in.a0;
-      if (in.a0 + e1 <= in.end) {
-#pragma unroll 4
-        for (int e = e0 + gt; e < e1; e += kGatherThreads) cp_async_gather(xs + e, x + col_s[e]);
-      } else {
-        for (int e = e0 + gt; e < e1; e += kGatherThreads) {
-          const int k = in.a0 + e;
-          cp_async_gather(xs + e, x + (k < in.end ? col_s[e] : __ldg(g.col + k)));
-        }
-      }
-      cp_async_arrive(&gathered[s]);
-    }
-    cp_async_wait_all();
-    return;
-  }
-
-  // -------------------------------------------------------------- compute warps
-  epi.init();
-  auto meta_of = [&](int b) {
-    TileMeta m{0u, 0u, 0u, 0u};
-    const int v = v0 + b * G;
-    const int ti = v * kTilesPerBlock + warp;
-    if (b < nbk && ti < g.tile_num) {
-      const uint64_t pol = policy_evict_first();
-      m.txs = __ldg(g.tile_x + ti);
-      m.txe = __ldg(g.tile_x + ti + 1);
-      m.tys = __ldg(g.tile_y + ti);
-      const int j = ti * kOmega + lane;
-      if (!(m.tys & kMsb) && j < g.lane_num) m.desc = ld_stream(g.lane_desc + j, pol);
-    }
-    return m;
-  };
   double p0 = 0.0, p1 = 0.0;
-  TileMeta meta = meta_of(0);
-  for (int b = 0; b < nbk; ++b) {
-    const int s = b % S;
-    const int v = v0 + b * G;
-    const TileMeta cur = meta;
-    meta = meta_of(b + 1);                       // next block's tile metadata
-    const uint32_t par = (uint32_t)((b / S) & 1);
-    const bool ok = mbar_wait_bounded(&gathered[s], par) && mbar_wait_bounded(&full[s], par);
-    const StageInfo in = info[s];
-    AT* s_y = sy(s);
-    if (ok)
-      for (int r = tid; r <= in.y_be - in.y_bs; r += kComputeThreads) s_y[r] = AT(0);
-    if (compute_sync_or(!ok)) {
+  int it = 0;
+  for (int v = blockIdx.x; v < g.nb; v += G, ++it) {
+    const int s = it & 1;
+    const uint32_t par = (it >> 1) & 1;
+
+    // tile metadata of this warp, loaded before the wait to hide latency
+    const int ti = v * kTilesPerBlock + warp;
+    const bool tile_ok = ti < g.tile_num;
+    uint32_t txs = 0, txe = 0, tys = 0, desc = 0;
+    const int j = ti * kOmega + lane;
+    if (tile_ok) {
+      txs = __ldg(g.tile_x + ti);
+      txe = __ldg(g.tile_x + ti + 1);
+      tys = __ldg(g.tile_y + ti);
+      if (!(tys & kMsb) && j < g.lane_num) desc = ld_stream(g.lane_desc + j, pol_stream);
+    }
+    // geometry for the copy issued at the end of this iteration
+    int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
+    const bool refill = (tid == 0) && (v + 2 * G < g.nb);
+    if (refill) geom_of(v + 2 * G, nxb, nxe, nyb, nye);
+
+    const bool ok = mbar_wait_bounded(&mbar[s], par);
+    if (__syncthreads_or(!ok)) {
+      // expired wait: record it, let this CTA's copies land (bounded), leave
       if (tid == 0) atomicOr(&g.red->err, 1);
+      mbar_wait_bounded(&mbar[s], par);
+      if (v + G < g.nb) mbar_wait_bounded(&mbar[s ^ 1], ((it + 1) >> 1) & 1);
       return;
     }
-    const VT* vs = sv(s);
-    const XT* xs = sx(s);
-    // a product of the block: staged index i = k - a0; the array's last values may be
-    // unstaged (only in the block holding them)
-    const bool tail = in.end < in.x_be;
-    auto prod = [&](int i) -> AT {
-      if (!tail || in.a0 + i < in.end) return static_cast<AT>(widen(vs[i])) * static_cast<AT>(xs[i]);
-      // unstaged tail: the index is clamped so that steps whose product is discarded
-      // (down steps, the lane's end) never read past the array
-      const VT w = vals[min(in.a0 + i, g.nnz - 1)];
-      return static_cast<AT>(widen(w)) * static_cast<AT>(xs[i]);
-    };
+    const StageInfo in = info[s];
+    AT* prod;
+    int pb;
+    if constexpr (ProdInVals<VT, AT>::value) {
+      prod = reinterpret_cast<AT*>(sv(s));
+      pb = in.a0v;
+    } else {
+      prod = reinterpret_cast<AT*>(sc(s));
+      pb = in.a0c;
+    }
 
-    const int ti = v * kTilesPerBlock + warp;
-    const int j = ti * kOmega + lane;
-    if (ti < g.tile_num && cur.txs < cur.txe) {
-      const int y_ws = (int)(cur.tys & ~kMsb);
-      AT* syt = s_y + (y_ws - in.y_bs);
-      const int i0 = (int)cur.txs - in.a0;        // staged index of the tile's first nonzero
-      if (cur.tys & kMsb) {
-        // single-row tile (tile_fast_tackle): plain warp reduction, no descriptor
-        AT sum = AT(0);
-        const int len = (int)(cur.txe - cur.txs);
+    // ---- stage products val * x[col] (load_smem of Algorithm MERBIT SpMV)
+    {
+      const int cnt = in.x_be - in.x_bs;
+      AT xv[kSigmaMax];
 #pragma unroll
-        for (int q = 0; q < kSigmaMax; ++q) {
-          const int k = lane + 32 * q;
-          if (k < len) sum += prod(i0 + k);
+      for (int u = 0; u < kSigmaMax; ++u) {
+        const int e = tid + u * kThreads;
+        xv[u] = AT(0);
+        if (e < cnt) {
+          const int k = in.x_bs + e;
+          const int c = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
+          xv[u] = static_cast<AT>(ld_x(x + c, pol_x));
         }
-        for (int k = lane + 32 * kSigmaMax; k < len; k += 32) sum += prod(i0 + k);
+      }
+#pragma unroll
+      for (int u = 0; u < kSigmaMax; ++u) {
+        const int e = tid + u * kThreads;
+        if (e < cnt) {
+          const int k = in.x_bs + e;
+          const AT v = static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
+          prod[k - pb] = v * xv[u];
+        }
+      }
+    }
+    AT* s_y = prod + (in.x_be - pb);
+    for (int r = tid; r <= in.y_be - in.y_bs; r += kThreads) s_y[r] = AT(0);
+    __syncthreads();
+
+    // ---- per-tile reduction (tile_fast_tackle / tile_normal_tackle + WarpSegmentedSum)
+    if (tile_ok && txs < txe) {
+      const int y_ws = (int)(tys & ~kMsb);
+      AT* sy = s_y + (y_ws - in.y_bs);
+      const AT* pt = prod + ((int)txs - pb);
+      if (tys & kMsb) {
+        // single-row tile: plain warp reduction, no descriptor
+        AT sum = AT(0);
+        for (int k = lane; k < (int)(txe - txs); k += 32) sum += pt[k];
         sum = warp_sum(sum);
-        if (lane == 0) atomicAdd(syt, sum);
+        if (lane == 0) atomicAdd(sy, sum);
       } else {
-        // tile_normal_tackle: sigma steps of this lane, driven by its descriptor
         const bool active = j < g.lane_num;
         const int lane_len = active ? min(g.sigma, g.steps - j * g.sigma) : 0;
         const uint32_t valid = (1u << lane_len) - 1u;
-        const uint32_t dm = (cur.desc >> 18) & valid;     // down steps
-        const uint32_t rm = ~(cur.desc >> 18) & valid;    // right steps
-        const int y0 = active ? (int)((cur.desc >> 9) & 511u) : (g.n_rows - y_ws);
-        const int il = i0 + (int)(cur.desc & 511u);       // staged index of the lane's first nonzero
-        // step k consumes nonzero k - (down steps before k): the addresses follow from
-        // the descriptor alone, so all loads are issued before any addition or flush
-        AT pv[kSigmaMax];
-#pragma unroll
-        for (int k = 0; k < kSigmaMax; ++k) pv[k] = prod(il + k - __popc(dm & ((1u << k) - 1u)));
+        const uint32_t dm = (desc >> 18) & valid;     // down steps
+        const uint32_t rm = ~(desc >> 18) & valid;    // right steps
+        const int y0 = active ? (int)((desc >> 9) & 511u) : (g.n_rows - y_ws);
+        const AT* pl = pt + (int)(desc & 511u);       // this lane's first product
         AT sum = AT(0);
 #pragma unroll
         for (int k = 0; k < kSigmaMax; ++k) {
+          // step k consumes product k - (down steps before k), an address that follows
+          // from the descriptor alone
           const int nd = __popc(dm & ((1u << k) - 1u));
+          const AT pv = pl[k - nd];
           if ((dm >> k) & 1u) {
             // down step: row y0 + nd ends here; only the lane's first such row can
             // have begun in an earlier lane, so only that one needs an atomic add
-            if (nd == 0) atomicAdd(syt + y0, sum);
-            else syt[y0 + nd] = sum;
+            if (nd == 0) atomicAdd(sy + y0, sum);
+            else sy[y0 + nd] = sum;
             sum = AT(0);
           } else if ((rm >> k) & 1u) {
-            sum += pv[k];
+            sum += pv;
           }
         }
         const int yo = y0 + __popc(dm);
         const bool head = lane == 0 || dm != 0u;
-        // WarpSegmentedSum: segmented inclusive scan of trailing sums; heads start segments
+        // segmented inclusive scan of trailing sums; heads start segments
         AT sv_ = sum;
         int f = head ? 1 : 0;
 #pragma unroll
@@ -571,23 +480,25 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             f = fu;
           }
         }
-        // a head lane adds the segment that ends just before it; lane 0 takes the
-        // tile's final segment (ending at lane 31)
+        // a head lane adds the segment that ends just before it; lane 0 takes
+        // the tile's final segment (ending at lane 31)
         const int src = lane == 0 ? 31 : lane - 1;
         const AT seg = __shfl_sync(0xffffffffu, sv_, src);
         const int row = __shfl_sync(0xffffffffu, yo, src);
-        if (head) atomicAdd(syt + row, seg);
+        if (head) atomicAdd(sy + row, seg);
       }
     }
-    compute_sync();
+    __syncthreads();
 
-    // block commit: interior rows complete here, boundary rows into FP64 accumulators
-    for (int r = in.y_bs + 1 + tid; r < in.y_be; r += kComputeThreads)
-      epi.row(r, s_y[r - in.y_bs], p0, p1);
+    // ---- block commit: interior rows complete here, boundary rows via FP64 accumulators
+    for (int r = in.y_bs + 1 + tid; r < in.y_be; r += kThreads) epi.row(r, s_y[r - in.y_bs], p0, p1);
     if (tid == 0) atomicAdd(g.bnd_acc + __ldg(g.bnd_slot + v), static_cast<double>(s_y[0]));
     if (tid == 32 && in.y_be != in.y_bs && in.y_be < g.n_rows)
       atomicAdd(g.bnd_acc + __ldg(g.bnd_slot + v + 1), static_cast<double>(s_y[in.y_be - in.y_bs]));
-    mbar_arrive(&empty[s]);                     // this thread is done with stage s
+    // stage s is free again once every thread is past this point
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (refill) issue(s, nxb, nxe, nyb, nye);
   }
 
   if constexpr (Epi::kReduce) {
@@ -597,15 +508,15 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
       red_smem[warp][0] = p0;
       red_smem[warp][1] = p1;
     }
-    compute_sync();
+    __syncthreads();
     if (tid == 0) {
-      double a = 0.0, b2 = 0.0;
+      double a = 0.0, b = 0.0;
 #pragma unroll
-      for (int w = 0; w < kComputeWarps; ++w) {
+      for (int w = 0; w < kThreads / 32; ++w) {
         a += red_smem[w][0];
-        b2 += red_smem[w][1];
+        b += red_smem[w][1];
       }
-      g.part[blockIdx.x] = make_double2(a, b2);
+      g.part[blockIdx.x] = make_double2(a, b);
     }
   }
 }
@@ -681,16 +592,15 @@ template <typename VT, typename XT, typename AT, typename Epi>
 cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, const Epi& epi,
                         cudaStream_t st) {
   if (p->nb == 0) return cudaSuccess;
-  constexpr int S = stages_for<VT, XT, AT>();
   auto kern = merbit_spmv_kernel<VT, XT, AT, Epi>;
-  const size_t smem = S * Layout<VT, XT, AT>(p->sigma).bytes;
-  const size_t smem_max = S * Layout<VT, XT, AT>(kSigmaMax).bytes;
-  int grid = persistent_grid(reinterpret_cast<const void*>(kern), kCtaThreads, smem, smem_max,
+  const size_t smem = 2 * stage_bytes<VT>(p->sigma);
+  const size_t smem_max = 2 * stage_bytes<VT>(kSigmaMax);
+  int grid = persistent_grid(reinterpret_cast<const void*>(kern), kThreads, smem, smem_max,
                              p->num_sms);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   if ((int64_t)grid > p->nb) grid = (int)p->nb;
   if (grid > kMaxParts) grid = kMaxParts;
-  kern<<<grid, kCtaThreads, smem, st>>>(p->geom(), vals, x, epi);
+  kern<<<grid, kThreads, smem, st>>>(p->geom(), vals, x, epi);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int fgrid = (int)std::min<int64_t>((p->nb + 1 + 255) / 256, (int64_t)p->num_sms * 4);
