@@ -207,6 +207,29 @@ merbit_status merbit_pagerank_ex(merbit_plan_t plan, merbit_dtype dtype, const v
                                  double* resid_out, double* resid_hist, int* launches_out,
                                  void* stream);
 
+/*
+ * merbit_spmv_noalloc — y = A x in f32 for callers that must not allocate
+ * device memory (the paper has no counterpart: it is an entry point of this
+ * library only).  Some callers cannot call cudaMalloc — code whose device
+ * memory belongs to another framework's pool, or paths where cudaMalloc's
+ * device-wide synchronisation is not acceptable.  This call builds the MERBIT
+ * schedule (sigma = 14) and runs the product without allocating anything: it
+ * uses the caller's row_ptr, col_idx, vals, x (n_cols entries) and y (n_rows
+ * entries, fully overwritten), all device pointers, plus a fixed scratch array
+ * compiled into the library (8 MiB; every GPU that loads the library keeps it
+ * until the process exits).  That is enough for matrices of up to about 27
+ * million rows plus nonzeros; larger ones are rejected with MERBIT_EINVAL and
+ * a message from merbit_last_error() (use merbit_plan / merbit_spmv).  The
+ * first call on a device looks up the scratch array's device address; make
+ * that first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (other streams, other threads) race and give
+ * wrong results.  Asynchronous on `stream`; vals and col_idx must be 16-byte
+ * aligned; row_ptr is trusted (not checked).  Errors: EINVAL, EOVERFLOW, ECUDA.
+ */
+merbit_status merbit_spmv_noalloc(const int32_t* row_ptr, const int32_t* col_idx, const float* vals,
+                                  const float* x, float* y, int64_t n_rows, int64_t n_cols,
+                                  int64_t nnz, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* merbit_last_error(void);
 

@@ -263,6 +263,12 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 }  // namespace
 
+namespace merbit {
+void set_last_error(const char* msg) {
+  std::snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+}  // namespace merbit
+
 // ============================================================================
 extern "C" {
 

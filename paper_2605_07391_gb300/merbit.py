@@ -26,8 +26,8 @@ _TORCH_DT = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch
 
 EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_get_info",
            "merbit_plan_sync", "merbit_plan_export", "merbit_spmv", "merbit_spmv_ex", "merbit_spmv_host",
-           "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_last_error",
-           "merbit_version"]
+           "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
+           "merbit_last_error", "merbit_version"]
 
 
 class MerbitError(RuntimeError):
