@@ -316,10 +316,12 @@ def main():
                         "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": alg_bytes,
                         "bytes_per_nnz": alg_bytes / a.nnz, "parts": alg_parts,
-                        "kernel": "merbit_spmv_kernel<float,float,float,EpiPlain>",
+                        "kernel": "merbit_spmv_kernel<float,float,float,EpiPlain> + merbit_finalize_kernel",
                         "mean_launch_ms": mean_launch_ms,
                         "median_launch_ms": statistics.median(launch_ms)},
-           "plan_ms": plan_ms, "gen_s": gen_s, "gpu_launches": K, "clocks": clock_info}
+           "plan_ms": plan_ms, "gen_s": gen_s,
+           # each step launches the SpMV kernel and its boundary-row finalize kernel
+           "gpu_launches": 2 * K, "clocks": clock_info}
 
     if rank == 0:
         # ---- end to end through the host-buffer entry point (pinned buffers)
