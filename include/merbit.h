@@ -140,6 +140,23 @@ merbit_status merbit_spmv_ex(merbit_plan_t plan, merbit_dtype vals_dtype, merbit
                              void* stream);
 
 /*
+ * merbit_spmm — Y = A X for k right-hand sides at once (the batching extension
+ * of the method: k personalisation vectors in one pass over the plan).  X is
+ * row-major n_cols x k with leading dimension ldx >= k, Y row-major n_rows x k
+ * with ldy >= k, all f32 device pointers; vals f32, 16-byte aligned.  Columns
+ * are processed in chunks of up to 32; each nonzero's column index and value are
+ * read once per chunk and the gathered row slice X[col, chunk] serves the whole
+ * chunk.  When k, ldx and ldy are multiples of 4 and X, Y are 16-byte aligned the
+ * slices are read as 16-byte vectors, otherwise element by element.  Y's first
+ * k columns are fully overwritten (rows of A with no nonzeros get 0).
+ * Asynchronous on `stream`; allocates (once per plan) a (block_num + 1) x 32
+ * FP64 accumulator for rows shared between blocks.  Errors: EINVAL (NULL
+ * pointers, k < 0, ldx < k, ldy < k, misaligned vals), ENOMEM, ECUDA.
+ */
+merbit_status merbit_spmm(merbit_plan_t plan, const float* vals, const float* X, float* Y,
+                          int64_t k, int64_t ldx, int64_t ldy, void* stream);
+
+/*
  * merbit_spmv_host — y = A x with x and y in HOST memory (pinned or pageable;
  * `vals` stays a device pointer).  x is copied into plan-owned device memory,
  * the product runs on `stream`, y is copied back, and the stream is

@@ -180,6 +180,15 @@ def spmv(row_ptr, col, val, x) -> tuple[np.ndarray, np.ndarray]:
     return y, d
 
 
+def spmm(row_ptr, col, val, X) -> tuple[np.ndarray, np.ndarray]:
+    """Y = A X for a dense X (n_cols x k): column j of Y is spmv() of column j of X.
+    Returns (Y, D) with D the per-entry scale sum_k |val[k] * X[col[k], j]|."""
+    X = np.asarray(X, np.float64)
+    cols = [spmv(row_ptr, col, val, X[:, j]) for j in range(X.shape[1])]
+    return (np.stack([c[0] for c in cols], axis=1) if cols else np.zeros((len(row_ptr) - 1, 0)),
+            np.stack([c[1] for c in cols], axis=1) if cols else np.zeros((len(row_ptr) - 1, 0)))
+
+
 def spmv_rows(row_ptr, col, val, x, rows) -> tuple[np.ndarray, np.ndarray]:
     """spmv() evaluated only at the listed rows (for sampled checks at full size)."""
     row_ptr = np.asarray(row_ptr, np.int64)

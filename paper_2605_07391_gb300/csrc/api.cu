@@ -68,6 +68,7 @@ void free_plan(merbit_plan_s* p) {
   cudaFree(p->hist);
   cudaFree(p->x_stage);
   cudaFree(p->y_stage);
+  cudaFree(p->spmm_acc);
   if (p->host_pinned) cudaFreeHost(p->host_pinned);
   delete p;
 }
@@ -449,6 +450,25 @@ merbit_status merbit_spmv(merbit_plan_t p, merbit_dtype dtype, const void* vals,
   if (dtype != MERBIT_F32 && dtype != MERBIT_F64)
     return fail(MERBIT_EINVAL, "merbit_spmv: dtype must be F32 or F64");
   return merbit_spmv_ex(p, dtype, dtype, vals, x, y, 0, nullptr);
+}
+
+merbit_status merbit_spmm(merbit_plan_t p, const float* vals, const float* X, float* Y, int64_t k,
+                          int64_t ldx, int64_t ldy, void* stream) {
+  if (merbit_status s = check_plan(p)) return s;
+  if (k < 0 || ldx < k || ldy < k) return fail(MERBIT_EINVAL, "need k >= 0, ldx >= k, ldy >= k");
+  if (k == 0 || p->n_rows == 0) return MERBIT_OK;
+  if (!Y || (p->nnz > 0 && (!vals || !X))) return fail(MERBIT_EINVAL, "vals, X or Y is NULL");
+  if (p->nnz > 0 && !aligned(vals, 16)) return fail(MERBIT_EINVAL, "vals must be 16-byte aligned");
+  if (!aligned(X, 4) || !aligned(Y, 4)) return fail(MERBIT_EINVAL, "X / Y must be 4-byte aligned");
+  if ((int64_t)p->n_cols * ldx >= ((int64_t)1 << 40)) return fail(MERBIT_EINVAL, "X too large");
+  cudaStream_t st = as_stream(stream);
+  if (!p->spmm_acc) {
+    const size_t bytes = sizeof(double) * 32 * (size_t)(p->nb + 1);
+    MB_TRY(cudaMalloc(&p->spmm_acc, bytes));
+    MB_TRY(cudaMemsetAsync(p->spmm_acc, 0, bytes, st));
+  }
+  MB_TRY(spmm_plain_f32(p, vals, X, k, ldx, Y, ldy, p->spmm_acc, st));
+  return MERBIT_OK;
 }
 
 merbit_status merbit_spmv_host(merbit_plan_t p, merbit_dtype dtype, const void* vals,

@@ -79,6 +79,7 @@ struct merbit_plan_s {
   void* y_stage = nullptr;
   size_t x_stage_bytes = 0, y_stage_bytes = 0;
   void* host_pinned = nullptr;           // small pinned block for state read-back
+  double* spmm_acc = nullptr;            // (nb + 1) x 32 FP64 boundary accumulators of the SpMM
 
   merbit::Geometry geom() const {
     merbit::Geometry g;
@@ -143,6 +144,10 @@ cudaError_t spmv_resid_f64(const merbit_plan_s* p, const double* vals, const dou
                            const ResidParams& prm, cudaStream_t st);
 cudaError_t spmv_sweep(const merbit_plan_s* p, merbit_dtype vdt, const void* vals,
                        const float* x, const SweepParams& prm, cudaStream_t st);
+// Y = A X, row-major X (n_cols x k, leading dimension ldx) and Y (n_rows x k, ldy), f32;
+// acc: (nb + 1) x 32 zeroed FP64 accumulators (left zeroed)
+cudaError_t spmm_plain_f32(const merbit_plan_s* p, const float* vals, const float* X, int64_t k,
+                           int64_t ldx, float* Y, int64_t ldy, double* acc, cudaStream_t st);
 // pi += delta (FP64) with delta = the refinement's latest inner iterate; s_out[1] = dangling mass
 cudaError_t ir_apply(const merbit_plan_s* p, double* pi, double* s_out, cudaStream_t st);
 

@@ -25,7 +25,8 @@ MODES = {"plain": PLAIN, "ir_bf16": IR_BF16, "ir_f16": IR_F16, "ir_f32": IR_F32}
 _TORCH_DT = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch.float16: F16}
 
 EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_get_info",
-           "merbit_plan_sync", "merbit_plan_export", "merbit_spmv", "merbit_spmv_ex", "merbit_spmv_host",
+           "merbit_plan_sync", "merbit_plan_export", "merbit_spmv", "merbit_spmv_ex", "merbit_spmm",
+           "merbit_spmv_host",
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
            "merbit_last_error", "merbit_version"]
 
@@ -74,6 +75,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_spmv": [vp, i32, vp, vp, vp],
             "merbit_spmv_ex": [vp, i32, i32, vp, vp, vp, i32, vp],
             "merbit_spmv_host": [vp, i32, vp, vp, vp, vp],
+            "merbit_spmm": [vp, vp, vp, vp, i64, i64, i64, vp],
             "merbit_vals_convert": [vp, i32, vp, i32, i64, i32, ctypes.POINTER(i32), vp],
             "merbit_pagerank": [vp, i32, vp, dbl, dbl, vp],
             "merbit_pagerank_ex": [vp, i32, vp, dbl, dbl, i32, i32, i32, dbl, vp,
@@ -209,6 +211,25 @@ def spmv(p: Plan, vals: torch.Tensor, x: torch.Tensor, y: torch.Tensor | None = 
     _check("merbit_spmv_ex", load().merbit_spmv_ex(p.handle, _dt(vals), xdt, _ptr(vals), _ptr(x),
                                                   _ptr(y), scale_exp, _stream(stream)))
     return y
+
+
+def spmm(p: Plan, vals: torch.Tensor, X: torch.Tensor, Y: torch.Tensor | None = None,
+         stream=None) -> torch.Tensor:
+    """merbit_spmm: Y = A X for a row-major X (n_cols x k); Y's first k columns overwritten."""
+    _need_cuda(vals, X, Y)
+    if X.dim() != 2 or X.dtype != torch.float32 or vals.dtype != torch.float32:
+        raise ValueError("spmm takes f32 vals and a 2-D f32 X")
+    if X.stride(1) != 1:
+        raise ValueError("X must be row-major")
+    k = X.shape[1]
+    if Y is None:
+        Y = torch.empty(p.n_rows, k, dtype=torch.float32, device=X.device)
+    if Y.stride(1) != 1:
+        raise ValueError("Y must be row-major")
+    _check("merbit_spmm", load().merbit_spmm(p.handle, _ptr(vals), ctypes.c_void_p(X.data_ptr()),
+                                            ctypes.c_void_p(Y.data_ptr()), k, X.stride(0),
+                                            Y.stride(0), _stream(stream)))
+    return Y
 
 
 def spmv_host(p: Plan, vals: torch.Tensor, x_host: torch.Tensor, y_host: torch.Tensor | None = None,

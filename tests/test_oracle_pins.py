@@ -188,6 +188,20 @@ def test_spmv_dense_bruteforce(seed):
     np.testing.assert_allclose(d, _dense_bruteforce(np.abs(dense), np.abs(x)), rtol=1e-14)
 
 
+def test_spmm_dense_bruteforce():
+    rng = np.random.default_rng(11)
+    a = inputs.random_sparse(40, 30, 0.2, 11, empty_frac=0.2)
+    dense = np.zeros((40, 30))
+    for r in range(40):
+        for k in range(a.row_ptr[r], a.row_ptr[r + 1]):
+            dense[r, a.col[k]] = a.val[k]
+    X = rng.standard_normal((30, 5))
+    Y, D = oracle.spmm(a.row_ptr, a.col, a.val, X)
+    ref = np.array([[sum(dense[i, j] * X[j, c] for j in range(30)) for c in range(5)] for i in range(40)])
+    np.testing.assert_allclose(Y, ref, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(D, np.abs(dense) @ np.abs(X), rtol=1e-13)
+
+
 def test_spmv_special_matrices():
     rng = np.random.default_rng(7)
     x = rng.standard_normal(50)
