@@ -211,6 +211,60 @@ def algorithmic_bytes_f32(a, tiles) -> tuple[int, dict]:
     return sum(parts.values()), {"r_f": float(marked.mean()) if marked.size else 0.0, **parts}
 
 
+def run_batched(args, dev, stream) -> dict:
+    """SpMM Y = A X (row-major X, k columns) per call and personalised PageRank (k one-hot
+    seeds over vertices with out-edges) to L1 residual 1e-6 per column, R-MAT scale 22."""
+    import torch
+
+    import inputs
+    import paper_2605_07391_gb300 as mb
+    a = inputs.rmat_transition(22, 16, 7)
+    rp = torch.from_numpy(a.row_ptr).to(dev)
+    col = torch.from_numpy(a.col).to(dev)
+    vals = torch.from_numpy(a.val).to(dev, torch.float32)
+    p = mb.plan(rp, col, a.n_rows, a.n_cols, stream=stream)
+    tiles = p.info()
+    hbm = peaks()[0]
+    res = {"workload": "rmat22_transition", "nnz": int(a.nnz), "n": int(a.n_rows)}
+    for k in (8, 32):
+        X = torch.rand(a.n_cols, k, device=dev)
+        Y = torch.empty(a.n_rows, k, device=dev)
+        for _ in range(5):
+            mb.spmm(p, vals, X, Y, stream=stream)
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        reps = 50
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            mb.spmm(p, vals, X, Y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        alg = 8 * a.nnz + 4 * k * (a.n_cols + a.n_rows) + 4 * tiles.lane_num + 8 * (tiles.tile_num + 1)
+        rec = {"spmm_ms": ms, "gnnz_vec_s": a.nnz * k / (ms * 1e-3) / 1e9,
+               "spmm_alg_gbs": alg / (ms * 1e-3) / 1e9, "spmm_roofline_frac": alg / (ms * 1e-3) / 1e9 / hbm,
+               "spmm_alg_bytes": alg}
+        del X, Y
+        seeds = inputs.ppr_seeds(a, k, 22)
+        mb.ppr(p, vals, seeds, 0.85, tol=0.0, max_iter=2, stream=stream)       # warm
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = mb.ppr(p, vals, seeds, 0.85, tol=1e-6, max_iter=300, stream=stream)
+        torch.cuda.synchronize(dev)
+        pms = (time.perf_counter() - t0) * 1e3
+        rec.update({"ppr_ms_to_1e-6": pms, "ppr_updates": r["iters"], "ppr_converged": r["converged"],
+                    "ppr_ms_per_update": pms / max(1, r["iters"]), "ppr_max_resid": max(r["resid"])})
+        if not args.no_oracle_check:
+            import oracle
+            Pi = r["pi"][:, [0, k - 1]].double().cpu().numpy()
+            rr = oracle.ppr_residual(a.row_ptr, a.col, a.val, Pi, [int(seeds[0]), int(seeds[k - 1])], 0.85)
+            rec["ppr_oracle_l1_residual_cols_0_last"] = [float(v) for v in rr]
+        res[f"k{k}"] = rec
+        del r
+    p.destroy()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,6 +275,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work (reference arm)")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work (cpu_baseline)")
     ap.add_argument("--no-pagerank", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched runs (SpMM and personalised PageRank, R-MAT scale 22)")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--inner-sweeps", type=int, default=32, help="max inner sweeps per refinement step")
     ap.add_argument("--sigma", type=int, default=14, help="steps per lane of the plan")
@@ -392,6 +448,10 @@ def main():
                 out["pagerank"]["mixed_vs_ir_f32_speedup"] = pr["ir_f32"]["ms"] / pr["ir_bf16"]["ms"]
             if pr["plain_f64"]["converged"]:
                 out["pagerank"]["mixed_vs_plain_f64_speedup"] = pr["plain_f64"]["ms"] / pr["ir_bf16"]["ms"]
+
+        # ---- batching: SpMM and personalised PageRank on R-MAT scale 22, k = 8 and 32
+        if not args.no_batched:
+            out["batched"] = run_batched(args, dev, stream)
 
         # ---- CPU baseline: the float64 oracle on a bounded sample
         nnz_done, t_used = oracle_sample_rate(a, args.cpu_budget, x64)

@@ -157,6 +157,28 @@ merbit_status merbit_spmm(merbit_plan_t plan, const float* vals, const float* X,
                           int64_t k, int64_t ldx, int64_t ldy, void* stream);
 
 /*
+ * merbit_ppr — personalised PageRank for k seed vertices at once, on the batched
+ * product (the batching extension of Sec. 5.5.1's power method).  Column c of the
+ * row-major n x k result Pi (device, leading dimension k, f32) is the stationary
+ * vector of
+ *     pi' = alpha P^T pi + (alpha D + 1 - alpha) e_{seeds[c]},
+ * D = the mass of pi on dangling vertices (empty columns of the plan's matrix), i.e.
+ * teleport and dangling mass both return to the seed.  Starts from pi_0 = e_seed and
+ * performs updates until every column's ||pi' - pi||_1 is below tol (tol <= 0: exactly
+ * max_iter updates).  The plan must be square; vals (f32 device, 16-byte aligned) are
+ * the values of P^T; seeds is a HOST array of k vertex ids, 1 <= k <= 1024.  Outputs (each may be
+ * NULL): iters_out = updates performed; resid_out (host, k entries) = each column's
+ * last ||pi' - pi||_1; resid_hist (host, max_iter entries) = per update the largest
+ * column residual.  Synchronous with respect to the host (it polls the device every 8
+ * updates); uses plan-owned device memory for a second n x k iterate.  Errors: EINVAL
+ * (bad arguments or seed), ENOTCONV (tol not reached; Pi holds the last iterate),
+ * EDEVICE (a kernel's bounded wait expired), ENOMEM, ECUDA.
+ */
+merbit_status merbit_ppr(merbit_plan_t plan, const float* vals, const int32_t* seeds, int64_t k,
+                         double alpha, double tol, int max_iter, float* Pi, int* iters_out,
+                         double* resid_out, double* resid_hist, void* stream);
+
+/*
  * merbit_spmv_host — y = A x with x and y in HOST memory (pinned or pageable;
  * `vals` stays a device pointer).  x is copied into plan-owned device memory,
  * the product runs on `stream`, y is copied back, and the stream is

@@ -270,6 +270,18 @@ def in_star(k: int) -> CSR:
     return from_edges(k + 1, [(i, 0) for i in range(1, k + 1)], f"instar{k}")
 
 
+def ppr_seeds(a: CSR, k: int, seed: int) -> np.ndarray:
+    """k distinct seed vertices drawn uniformly from the vertices with at least one
+    out-edge (non-empty columns of the transition matrix P^T), as int32."""
+    has_out = np.zeros(a.n_cols, bool)
+    has_out[np.asarray(a.col, np.int64)] = True
+    cand = np.flatnonzero(has_out)
+    if cand.size < k:
+        raise ValueError(f"only {cand.size} vertices have out-edges, {k} seeds asked")
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(cand, size=k, replace=False)).astype(np.int32)
+
+
 def random_graph_transition(n: int, p: float, seed: int) -> CSR:
     """Small directed graph, each ordered pair (s != t) an edge w.p. p."""
     rng = np.random.default_rng(seed)

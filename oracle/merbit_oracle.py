@@ -9,8 +9,9 @@ import it.  It shares no code with the CUDA library and never imports it.
 Pinned by ``tests/test_oracle_pins.py`` against: the paper's worked-example
 counts (Sec. 4.1.1), a literal step-by-step merge-path walk on tiny inputs,
 path invariants, dense brute-force SpMV, closed-form PageRank vectors (n-cycle,
-bidirected star, in-star, 3-chain), a dense linear solve of the PageRank
-fixed-point equation, and numpy's IEEE half conversion for the rounding helper.
+bidirected star, in-star, 3-chain), closed-form personalised vectors (n-cycle,
+chain ending in a dangling vertex, bidirected star), dense linear solves of both
+fixed-point equations, and numpy's IEEE half conversion for the rounding helper.
 
 Readings of points the paper leaves open (each is also listed in the design
 notes):
@@ -24,6 +25,8 @@ notes):
     columns of P^T and their mass is spread uniformly; the iteration is
     pi' = alpha P^T pi + (alpha D + 1 - alpha)/n with D the dangling mass, and
     it stops when ||pi' - pi||_1 < tol (Sec. 5.5.1 leaves the rule open).
+  * Personalised PageRank (the batching extension): one column per seed s, the
+    teleport vector is e_s and the dangling mass also returns to s; pi_0 = e_s.
 """
 from __future__ import annotations
 
@@ -275,6 +278,64 @@ def pagerank_dense_solve(dense_pt: np.ndarray, alpha: float = 0.85) -> np.ndarra
     M = np.eye(n) - alpha * dense_pt - (alpha / n) * np.outer(np.ones(n), d.astype(np.float64))
     b = np.full(n, (1.0 - alpha) / n)
     return np.linalg.solve(M, b)
+
+
+def ppr_step(row_ptr, col, val, Pi, alpha, dangling, seeds) -> np.ndarray:
+    """One personalised power step for every column c of Pi (n x k):
+    Pi'[:, c] = alpha P^T Pi[:, c] + (alpha D_c + 1 - alpha) e_{seeds[c]},
+    D_c the mass of Pi[:, c] on dangling vertices (teleport and dangling mass go to the seed)."""
+    Y, _ = spmm(row_ptr, col, val, Pi)
+    Y = alpha * Y
+    D = Pi[dangling].sum(axis=0)
+    for c, s in enumerate(seeds):
+        Y[s, c] += alpha * D[c] + (1.0 - alpha)
+    return Y
+
+
+def personalized_pagerank(row_ptr, col, val, seeds, alpha: float = 0.85, tol: float = 1e-10,
+                          max_iter: int = 1000, fixed_iters: int | None = None) -> dict:
+    """Power method per seed from Pi_0 = [e_s ...]; stops when every column's
+    ||pi' - pi||_1 < tol, or after exactly ``fixed_iters`` updates.  Returns Pi (n x k),
+    the number of updates, the per-update largest column residual and the last
+    per-column residuals."""
+    n = np.asarray(row_ptr).size - 1
+    seeds = [int(s) for s in seeds]
+    dangling = dangling_mask(n, col)
+    Pi = np.zeros((n, len(seeds)))
+    for c, s in enumerate(seeds):
+        Pi[s, c] = 1.0
+    hist, last = [], np.zeros(len(seeds))
+    iters = fixed_iters if fixed_iters is not None else max_iter
+    for _ in range(iters):
+        nxt = ppr_step(row_ptr, col, val, Pi, alpha, dangling, seeds)
+        last = np.abs(nxt - Pi).sum(axis=0)
+        hist.append(float(last.max()))
+        Pi = nxt
+        if fixed_iters is None and hist[-1] < tol:
+            break
+    return {"pi": Pi, "iters": len(hist), "resid": hist, "last": last}
+
+
+def ppr_residual(row_ptr, col, val, Pi, seeds, alpha: float = 0.85) -> np.ndarray:
+    """Per column, ||b_s - M_s pi||_1 with M_s = I - alpha P^T - alpha e_s d^T and
+    b_s = (1 - alpha) e_s (d the dangling indicator): the L1 size of one personalised
+    power step taken from pi."""
+    Pi = np.asarray(Pi, np.float64)
+    n = Pi.shape[0]
+    dangling = dangling_mask(n, col)
+    return np.abs(ppr_step(row_ptr, col, val, Pi, alpha, dangling, seeds) - Pi).sum(axis=0)
+
+
+def ppr_dense_solve(dense_pt: np.ndarray, seed: int, alpha: float = 0.85) -> np.ndarray:
+    """Fixed point of the personalised step as a linear system (n <= 64):
+    (I - alpha P^T - alpha e_s d^T) pi = (1 - alpha) e_s."""
+    dense_pt = np.asarray(dense_pt, np.float64)
+    n = dense_pt.shape[0]
+    d = ~np.any(dense_pt != 0, axis=0)
+    e = np.zeros(n)
+    e[seed] = 1.0
+    M = np.eye(n) - alpha * dense_pt - alpha * np.outer(e, d.astype(np.float64))
+    return np.linalg.solve(M, (1.0 - alpha) * e)
 
 
 def relative_linf_error(pi, pi_star) -> float:

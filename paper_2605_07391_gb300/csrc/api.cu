@@ -262,6 +262,15 @@ merbit_status ensure_hist(merbit_plan_s* p, size_t launches) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// (block_num + 1) x 32 zeroed FP64 accumulators of the SpMM's block-shared rows
+merbit_status ensure_spmm_acc(merbit_plan_s* p, cudaStream_t st) {
+  if (p->spmm_acc) return MERBIT_OK;
+  const size_t bytes = sizeof(double) * 32 * (size_t)(p->nb + 1);
+  MB_TRY(cudaMalloc(&p->spmm_acc, bytes));
+  MB_TRY(cudaMemsetAsync(p->spmm_acc, 0, bytes, st));
+  return MERBIT_OK;
+}
+
 }  // namespace
 
 namespace merbit {
@@ -462,12 +471,80 @@ merbit_status merbit_spmm(merbit_plan_t p, const float* vals, const float* X, fl
   if (!aligned(X, 4) || !aligned(Y, 4)) return fail(MERBIT_EINVAL, "X / Y must be 4-byte aligned");
   if ((int64_t)p->n_cols * ldx >= ((int64_t)1 << 40)) return fail(MERBIT_EINVAL, "X too large");
   cudaStream_t st = as_stream(stream);
-  if (!p->spmm_acc) {
-    const size_t bytes = sizeof(double) * 32 * (size_t)(p->nb + 1);
-    MB_TRY(cudaMalloc(&p->spmm_acc, bytes));
-    MB_TRY(cudaMemsetAsync(p->spmm_acc, 0, bytes, st));
-  }
+  if (merbit_status s = ensure_spmm_acc(p, st)) return s;
   MB_TRY(spmm_plain_f32(p, vals, X, k, ldx, Y, ldy, p->spmm_acc, st));
+  return MERBIT_OK;
+}
+
+merbit_status merbit_ppr(merbit_plan_t p, const float* vals, const int32_t* seeds, int64_t k,
+                         double alpha, double tol, int max_iter, float* Pi, int* iters_out,
+                         double* resid_out, double* resid_hist, void* stream) {
+  if (merbit_status s = check_plan(p)) return s;
+  if (p->n_rows != p->n_cols) return fail(MERBIT_EINVAL, "personalised PageRank needs a square plan");
+  if (!(alpha >= 0.0 && alpha < 1.0)) return fail(MERBIT_EINVAL, "alpha must be in [0, 1)");
+  if (max_iter < 1) return fail(MERBIT_EINVAL, "max_iter must be >= 1");
+  if (k < 1 || k > 1024) return fail(MERBIT_EINVAL, "k must be in [1, 1024]");
+  if (p->n_rows == 0) return fail(MERBIT_EINVAL, "the graph has no vertices");
+  if (!seeds || !Pi) return fail(MERBIT_EINVAL, "seeds or Pi is NULL");
+  if (p->nnz > 0 && !vals) return fail(MERBIT_EINVAL, "vals is NULL");
+  if (p->nnz > 0 && !aligned(vals, 16)) return fail(MERBIT_EINVAL, "vals must be 16-byte aligned");
+  if (!aligned(Pi, 4)) return fail(MERBIT_EINVAL, "Pi must be 4-byte aligned");
+  const int64_t n = p->n_rows;
+  if (n * k >= ((int64_t)1 << 40)) return fail(MERBIT_EINVAL, "n * k too large");
+  for (int64_t c = 0; c < k; ++c)
+    if (seeds[c] < 0 || seeds[c] >= n) return fail(MERBIT_EINVAL, "seed %lld out of range", (long long)c);
+  cudaStream_t st = as_stream(stream);
+  if (merbit_status s = ensure_dangling(p, st)) return s;
+  if (merbit_status s = ensure_hist(p, (size_t)max_iter)) return s;
+  if (merbit_status s = ensure_spmm_acc(p, st)) return s;
+  // scratch: second iterate | seeds | D per column | 2k accumulators | last residuals
+  const size_t xb = align256(sizeof(float) * (size_t)n * (size_t)k);
+  const size_t sb = align256(sizeof(int32_t) * (size_t)k);
+  const size_t db = align256(sizeof(double) * (size_t)k);
+  MB_TRY(grow(&p->scratch, &p->scratch_bytes, xb + sb + 4 * db));
+  char* base = static_cast<char*>(p->scratch);
+  float* x1 = reinterpret_cast<float*>(base);
+  int32_t* seed_d = reinterpret_cast<int32_t*>(base + xb);
+  double* d_cur = reinterpret_cast<double*>(base + xb + sb);
+  double* rd = reinterpret_cast<double*>(base + xb + sb + db);
+  double* last_r = reinterpret_cast<double*>(base + xb + sb + 3 * db);
+  MB_TRY(cudaMemcpyAsync(seed_d, seeds, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
+  MB_TRY(reset_device_state(p, st));
+  MB_TRY(cudaMemsetAsync(rd, 0, 2 * sizeof(double) * (size_t)k, st));
+  MB_TRY(ppr_init(p, Pi, k, seed_d, d_cur, st));
+  float* buf[2] = {Pi, x1};
+  const int kBatch = 8;
+  int it = 0;
+  StateWord w{};
+  while (it < max_iter) {
+    const int stop = std::min(max_iter, it + kBatch);
+    for (; it < stop; ++it) {
+      cudaError_t e = ppr_update(p, vals, buf[it & 1], buf[(it + 1) & 1], k, seed_d, d_cur, rd,
+                                 last_r, (float)alpha, tol, it, p->hist, p->spmm_acc, st);
+      if (e != cudaSuccess) return cuda_fail(e, "personalised PageRank launch");
+    }
+    MB_TRY(read_state(p, st, &w));
+    if (w.err || w.done) break;
+  }
+  if (w.err) {
+    MB_TRY(reset_device_state(p, st));
+    MB_TRY(cudaStreamSynchronize(st));
+    return fail(MERBIT_EDEVICE, "a kernel reported error bits 0x%x", w.err);
+  }
+  const int iters = w.done ? w.iters : max_iter;
+  if (iters & 1)
+    MB_TRY(cudaMemcpyAsync(Pi, x1, sizeof(float) * (size_t)n * (size_t)k, cudaMemcpyDeviceToDevice, st));
+  std::vector<double> h((size_t)iters);
+  MB_TRY(cudaMemcpyAsync(h.data(), p->hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (resid_out)
+    MB_TRY(cudaMemcpyAsync(resid_out, last_r, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, st));
+  MB_TRY(cudaStreamSynchronize(st));
+  if (iters_out) *iters_out = iters;
+  if (resid_hist)
+    for (int i = 0; i < iters; ++i) resid_hist[i] = h[(size_t)i];
+  if (tol > 0 && !w.done)
+    return fail(MERBIT_ENOTCONV, "personalised PageRank did not reach tol %.3g in %d updates "
+                "(largest residual %.3g)", tol, max_iter, iters > 0 ? h[(size_t)iters - 1] : 0.0);
   return MERBIT_OK;
 }
 

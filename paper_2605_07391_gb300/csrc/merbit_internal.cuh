@@ -148,6 +148,20 @@ cudaError_t spmv_sweep(const merbit_plan_s* p, merbit_dtype vdt, const void* val
 // acc: (nb + 1) x 32 zeroed FP64 accumulators (left zeroed)
 cudaError_t spmm_plain_f32(const merbit_plan_s* p, const float* vals, const float* X, int64_t k,
                            int64_t ldx, float* Y, int64_t ldy, double* acc, cudaStream_t st);
+// Y = scale * A X, skipped once the plan's stop flag is set (iterative drivers)
+cudaError_t spmm_scaled_f32(const merbit_plan_s* p, const float* vals, const float* X, int64_t k,
+                            int64_t ldx, float* Y, int64_t ldy, float scale, double* acc,
+                            cudaStream_t st);
+// Personalised PageRank: X = one-hot seed columns (n x k, ld k), d_cur = their dangling mass
+cudaError_t ppr_init(const merbit_plan_s* p, float* X, int64_t k, const int32_t* seed,
+                     double* d_cur, cudaStream_t st);
+// one update Y = alpha P^T X + (alpha D + 1 - alpha) e_seed for all k columns, then the
+// finish step (per-column residuals into last_r, D of Y into d_cur, hist[iter] = largest
+// residual, stop flag when it is below tol); rd: 2k zeroed FP64 accumulators (left zeroed)
+cudaError_t ppr_update(const merbit_plan_s* p, const float* vals, const float* X, float* Y,
+                       int64_t k, const int32_t* seed, double* d_cur, double* rd, double* last_r,
+                       float alpha, double tol, int iter, double* hist, double* acc,
+                       cudaStream_t st);
 // pi += delta (FP64) with delta = the refinement's latest inner iterate; s_out[1] = dangling mass
 cudaError_t ir_apply(const merbit_plan_s* p, double* pi, double* s_out, cudaStream_t st);
 

@@ -1,6 +1,6 @@
-// Host side of the batched product Y = A X (row-major X and Y, f32): column
-// chunks of 32, 16 or 8 through merbit_spmm_kernel, with 16-byte row slices
-// when every slice is 16-byte aligned and scalar slices otherwise.
+// Host side of the batched product Y = scale * A X (row-major X and Y, f32): column
+// chunks of 32, 16 or 8 through merbit_spmm_kernel, with 16-byte row slices when every
+// slice is 16-byte aligned and scalar slices otherwise.
 #include "spmm_kernel.cuh"
 
 namespace merbit {
@@ -9,12 +9,13 @@ namespace {
 
 template <int VW>
 cudaError_t spmm_chunks(const merbit_plan_s* p, const float* vals, const float* X, int64_t k,
-                        int64_t ldx, float* Y, int64_t ldy, double* acc, cudaStream_t st) {
+                        int64_t ldx, float* Y, int64_t ldy, float scale, bool gated, double* acc,
+                        cudaStream_t st) {
   for (int64_t c0 = 0; c0 < k;) {
     const int64_t left = k - c0;
     const int kc = left >= 32 ? 32 : left > 8 ? 16 : 8;
     SpmmGeometry sg{acc, (int)std::min<int64_t>(left, kc)};
-    EpiSpmmPlain epi{Y + c0, (int)ldy};
+    EpiSpmmPlain epi{Y + c0, (int)ldy, scale, gated};
     cudaError_t e;
     if (kc == 32) e = launch_spmm<32, VW>(p, vals, X + c0, (int)ldx, sg, epi, st);
     else if (kc == 16) e = launch_spmm<16, VW>(p, vals, X + c0, (int)ldx, sg, epi, st);
@@ -25,15 +26,27 @@ cudaError_t spmm_chunks(const merbit_plan_s* p, const float* vals, const float* 
   return cudaSuccess;
 }
 
+cudaError_t spmm_dispatch(const merbit_plan_s* p, const float* vals, const float* X, int64_t k,
+                          int64_t ldx, float* Y, int64_t ldy, float scale, bool gated, double* acc,
+                          cudaStream_t st) {
+  const bool vec = k % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 &&
+                   (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+  return vec ? spmm_chunks<4>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st)
+             : spmm_chunks<1>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st);
+}
+
 }  // namespace
 
 cudaError_t spmm_plain_f32(const merbit_plan_s* p, const float* vals, const float* X, int64_t k,
                            int64_t ldx, float* Y, int64_t ldy, double* acc, cudaStream_t st) {
-  const bool vec = k % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 &&
-                   (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
-                   (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
-  return vec ? spmm_chunks<4>(p, vals, X, k, ldx, Y, ldy, acc, st)
-             : spmm_chunks<1>(p, vals, X, k, ldx, Y, ldy, acc, st);
+  return spmm_dispatch(p, vals, X, k, ldx, Y, ldy, 1.f, false, acc, st);
+}
+
+cudaError_t spmm_scaled_f32(const merbit_plan_s* p, const float* vals, const float* X, int64_t k,
+                            int64_t ldx, float* Y, int64_t ldy, float scale, double* acc,
+                            cudaStream_t st) {
+  return spmm_dispatch(p, vals, X, k, ldx, Y, ldy, scale, true, acc, st);
 }
 
 }  // namespace merbit

@@ -36,6 +36,8 @@ template <> struct SpmmVec<1> {
   using T = float;
   static __device__ __forceinline__ T zero() { return 0.f; }
   static __device__ __forceinline__ T load(const float* p) { return __ldg(p); }
+  static __device__ __forceinline__ T load_plain(const float* p) { return *p; }
+  static __device__ __forceinline__ void store(float* p, const float (&a)[1]) { *p = a[0]; }
   static __device__ __forceinline__ void fma(float w, const T& x, T& s) { s = fmaf(w, x, s); }
   static __device__ __forceinline__ float get(const T& v, int) { return v; }
   static __device__ __forceinline__ T from(const float (&a)[1]) { return a[0]; }
@@ -49,6 +51,12 @@ template <> struct SpmmVec<4> {
   static __device__ __forceinline__ T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ T load(const float* p) {
     return __ldg(reinterpret_cast<const float4*>(p));
+  }
+  static __device__ __forceinline__ T load_plain(const float* p) {
+    return *reinterpret_cast<const float4*>(p);
+  }
+  static __device__ __forceinline__ void store(float* p, const float (&a)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
   }
   static __device__ __forceinline__ void fma(float w, const T& x, T& s) {
     s.x = fmaf(w, x.x, s.x);
@@ -71,20 +79,27 @@ template <> struct SpmmVec<4> {
   }
 };
 
-// Y[r, c..c+VW) of one column chunk: row() for a row summed in f32, row64 for one column of a
-// row summed in FP64 (block-shared rows).
+// Epilogue of the SpMM: Y[r, c..c+VW) = scale * (A X)[r, c..c+VW).  row() takes f32 row sums
+// (called by the thread owning columns c..c+VW), row64 one column of a block-shared row
+// summed in FP64 (finalize kernel).  A gated launch does nothing once an iterative driver
+// has set the plan's stop flag (launches queued after convergence).
 struct EpiSpmmPlain {
-  static constexpr bool kReduce = false;
   float* y;
   int ldy;
-  __device__ __forceinline__ void init() {}
-  __device__ __forceinline__ bool skip(const RedState*) const { return false; }
-  __device__ __forceinline__ void row(int r, int c, float s) const { y[(size_t)r * ldy + c] = s; }
+  float scale;
+  bool gated;
+  __device__ __forceinline__ bool skip(const RedState* red) const {
+    return gated && *reinterpret_cast<const volatile int*>(&red->done) != 0;
+  }
+  __device__ __forceinline__ void row(int r, int c, float s) const {
+    y[(size_t)r * ldy + c] = scale * s;
+  }
   __device__ __forceinline__ void row(int r, int c, const float4& s) const {
-    *reinterpret_cast<float4*>(y + (size_t)r * ldy + c) = s;
+    *reinterpret_cast<float4*>(y + (size_t)r * ldy + c) =
+        make_float4(scale * s.x, scale * s.y, scale * s.z, scale * s.w);
   }
   __device__ __forceinline__ void row64(int r, int c, double s) const {
-    y[(size_t)r * ldy + c] = static_cast<float>(s);
+    y[(size_t)r * ldy + c] = static_cast<float>(static_cast<double>(scale) * s);
   }
 };
 
@@ -120,7 +135,6 @@ __global__ void __launch_bounds__(kThreads, 3)
   const bool c_ok = c < sg.kc;
   const int G = gridDim.x;
   if (epi.skip(g.red)) return;
-  epi.init();
 
   const size_t svb = stage_vals_bytes<float>(g.sigma);
   const size_t stb = stage_bytes<float>(g.sigma);
@@ -404,7 +418,6 @@ template <int KC, typename Epi>
 __global__ void __launch_bounds__(256) merbit_spmm_finalize_kernel(const Geometry g,
                                                                    const SpmmGeometry sg, Epi epi) {
   if (epi.skip(g.red)) return;
-  epi.init();
   const int stride = gridDim.x * blockDim.x;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (g.nb + 1) * KC; p += stride) {
     const int k = p / KC, cc = p % KC;

@@ -26,7 +26,7 @@ _TORCH_DT = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch
 
 EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_get_info",
            "merbit_plan_sync", "merbit_plan_export", "merbit_spmv", "merbit_spmv_ex", "merbit_spmm",
-           "merbit_spmv_host",
+           "merbit_ppr", "merbit_spmv_host",
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
            "merbit_last_error", "merbit_version"]
 
@@ -76,6 +76,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_spmv_ex": [vp, i32, i32, vp, vp, vp, i32, vp],
             "merbit_spmv_host": [vp, i32, vp, vp, vp, vp],
             "merbit_spmm": [vp, vp, vp, vp, i64, i64, i64, vp],
+            "merbit_ppr": [vp, vp, vp, i64, dbl, dbl, i32, vp, ctypes.POINTER(i32),
+                           ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp],
             "merbit_vals_convert": [vp, i32, vp, i32, i64, i32, ctypes.POINTER(i32), vp],
             "merbit_pagerank": [vp, i32, vp, dbl, dbl, vp],
             "merbit_pagerank_ex": [vp, i32, vp, dbl, dbl, i32, i32, i32, dbl, vp,
@@ -230,6 +232,30 @@ def spmm(p: Plan, vals: torch.Tensor, X: torch.Tensor, Y: torch.Tensor | None = 
                                             ctypes.c_void_p(Y.data_ptr()), k, X.stride(0),
                                             Y.stride(0), _stream(stream)))
     return Y
+
+
+def ppr(p: Plan, vals: torch.Tensor, seeds, alpha: float = 0.85, tol: float = 1e-6,
+        max_iter: int = 1000, Pi: torch.Tensor | None = None, stream=None) -> dict:
+    """merbit_ppr: personalised PageRank for the given seed vertices (one column each).
+    Returns {"pi": n x k tensor, "iters", "resid" (per column), "hist", "converged"}."""
+    _need_cuda(vals, Pi)
+    if vals.dtype != torch.float32:
+        raise ValueError("ppr takes f32 vals")
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32))
+    k = int(seeds.size)
+    if Pi is None:
+        Pi = torch.empty(p.n_rows, k, dtype=torch.float32, device=vals.device)
+    if Pi.dtype != torch.float32 or tuple(Pi.shape) != (p.n_rows, k) or not Pi.is_contiguous():
+        raise ValueError("Pi must be a contiguous f32 n x k tensor")
+    iters = ctypes.c_int(0)
+    resid = (ctypes.c_double * max(k, 1))()
+    hist = (ctypes.c_double * max_iter)()
+    st = _check("merbit_ppr", load().merbit_ppr(
+        p.handle, _ptr(vals), seeds.ctypes.data_as(ctypes.c_void_p), k, alpha, tol, max_iter,
+        ctypes.c_void_p(Pi.data_ptr()), ctypes.byref(iters), resid, hist, _stream(stream)),
+        allow=(5,))
+    return {"pi": Pi, "iters": iters.value, "resid": [resid[i] for i in range(k)],
+            "hist": [hist[i] for i in range(iters.value)], "converged": st == 0}
 
 
 def spmv_host(p: Plan, vals: torch.Tensor, x_host: torch.Tensor, y_host: torch.Tensor | None = None,

@@ -323,6 +323,86 @@ def test_pagerank_invariants_rmat14():
                                               oracle.dangling_mask(n, a.col)) - pi).sum()) < 1e-15
 
 
+# Personalised PageRank (one column per seed; teleport and dangling mass go to the seed)
+
+def _ppr(a, seeds, **kw):
+    return oracle.personalized_pagerank(a.row_ptr, a.col, a.val, seeds, ALPHA, **kw)
+
+
+@pytest.mark.parametrize("n", [1, 5, 16])
+def test_ppr_cycle_closed_form(n):
+    """Directed n-cycle: pi_s[s + j] = (1 - a) a^j / (1 - a^n)."""
+    a = inputs.cycle_graph(n)
+    seeds = [0, 2 % n, n - 1]
+    Pi = _ppr(a, seeds, tol=1e-15)["pi"]
+    for c, s in enumerate(seeds):
+        ref = np.zeros(n)
+        for j in range(n):
+            ref[(s + j) % n] = (1 - ALPHA) * ALPHA ** j / (1 - ALPHA ** n)
+        np.testing.assert_allclose(Pi[:, c], ref, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("L", [2, 6])
+def test_ppr_chain_with_dangling_end(L):
+    """0 -> 1 -> ... -> L-1, the last vertex dangling: its mass returns to the seed, so
+    from seed m the chain behaves like a cycle of length L - m and vertices before m get 0."""
+    a = inputs.from_edges(L, [(i, i + 1) for i in range(L - 1)], f"chain{L}")
+    assert oracle.dangling_mask(L, a.col).tolist() == [False] * (L - 1) + [True]
+    seeds = list(range(L))
+    Pi = _ppr(a, seeds, tol=1e-15)["pi"]
+    for c, m in enumerate(seeds):
+        ref = np.zeros(L)
+        for j in range(L - m):
+            ref[m + j] = (1 - ALPHA) * ALPHA ** j / (1 - ALPHA ** (L - m))
+        np.testing.assert_allclose(Pi[:, c], ref, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("k", [1, 4, 9])
+def test_ppr_bidirected_star_closed_form(k):
+    """Centre 0 and leaves 1..k linked both ways.  Seed = leaf 1: centre a/(1+a), seed
+    (1-a) + a^2/((1+a)k), other leaves a^2/((1+a)k).  Seed = centre: 1/(1+a), leaves a/((1+a)k)."""
+    a = inputs.bidirected_star(k)
+    Pi = _ppr(a, [1, 0], tol=1e-15)["pi"]
+    c = ALPHA / (1 + ALPHA)
+    leaf = ALPHA * c / k
+    np.testing.assert_allclose(Pi[:, 0], [c, 1 - ALPHA + leaf] + [leaf] * (k - 1), rtol=1e-12)
+    np.testing.assert_allclose(Pi[:, 1], [1 / (1 + ALPHA)] + [ALPHA / ((1 + ALPHA) * k)] * k,
+                               rtol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_ppr_matches_dense_solve(seed):
+    a = inputs.random_graph_transition(20 + 9 * seed, 0.07, seed)
+    dense = np.zeros((a.n_rows, a.n_cols))
+    for r in range(a.n_rows):
+        for k in range(a.row_ptr[r], a.row_ptr[r + 1]):
+            dense[r, a.col[k]] = a.val[k]
+    dang = oracle.dangling_mask(a.n_rows, a.col)
+    seeds = [0, int(np.flatnonzero(dang)[0]) if dang.any() else 1, a.n_rows - 1]
+    Pi = _ppr(a, seeds, tol=1e-15)["pi"]
+    for c, s in enumerate(seeds):
+        ref = oracle.ppr_dense_solve(dense, s, ALPHA)
+        np.testing.assert_allclose(Pi[:, c], ref, rtol=1e-10, atol=1e-15)
+        assert oracle.ppr_residual(a.row_ptr, a.col, a.val, ref[:, None], [s], ALPHA)[0] < 1e-14
+
+
+def test_ppr_invariants_rmat14():
+    a = inputs.rmat_transition(14, 16, 1)
+    seeds = inputs.ppr_seeds(a, 8, 3)
+    dang = oracle.dangling_mask(a.n_rows, a.col)
+    assert len(set(seeds.tolist())) == 8 and not dang[seeds].any()
+    r = _ppr(a, seeds, fixed_iters=40)
+    Pi = r["pi"]
+    np.testing.assert_allclose(Pi.sum(axis=0), 1.0, atol=1e-12)     # mass conservation
+    assert Pi.min() >= 0.0
+    assert np.all(Pi[seeds, np.arange(8)] >= 1 - ALPHA)              # teleport lands on the seed
+    h = np.array(r["resid"])
+    assert np.all(h[1:] <= ALPHA * h[:-1] * (1 + 1e-9) + 1e-15)       # L1 contraction
+    np.testing.assert_allclose(oracle.ppr_residual(a.row_ptr, a.col, a.val, Pi, seeds, ALPHA),
+                               np.abs(oracle.ppr_step(a.row_ptr, a.col, a.val, Pi, ALPHA, dang, seeds)
+                                      - Pi).sum(axis=0), rtol=1e-14)
+
+
 def test_relative_linf_error():
     assert oracle.relative_linf_error([1.0, 2.2], [1.0, 2.0]) == pytest.approx(0.1)
 
