@@ -226,7 +226,7 @@ def run_batched(args, dev, stream) -> dict:
     tiles = p.info()
     hbm = peaks()[0]
     res = {"workload": "rmat22_transition", "nnz": int(a.nnz), "n": int(a.n_rows)}
-    for k in (8, 32):
+    for k in args.batched_k:
         X = torch.rand(a.n_cols, k, device=dev)
         Y = torch.empty(a.n_rows, k, device=dev)
         for _ in range(5):
@@ -277,6 +277,8 @@ def main():
     ap.add_argument("--no-pagerank", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched runs (SpMM and personalised PageRank, R-MAT scale 22)")
+    ap.add_argument("--batched-k", type=int, nargs="+", default=[8, 32],
+                    help="numbers of right-hand sides / seeds of the batched runs")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--inner-sweeps", type=int, default=32, help="max inner sweeps per refinement step")
     ap.add_argument("--sigma", type=int, default=14, help="steps per lane of the plan")
