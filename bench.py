@@ -265,6 +265,64 @@ def run_batched(args, dev, stream) -> dict:
     return res
 
 
+def run_autograd(args, dev, stream) -> dict:
+    """dL/dvals for L = sum_i w_i pi_i (w ~ N(0, 1)) at the PageRank fixed point of the R-MAT
+    scale 20 transition matrix, FP32: transpose + its plan (once per pattern), forward
+    PageRank to 1e-7, backward = gather of the transposed values + adjoint solve to 1e-6
+    relative + per-nonzero products; the FP32 gradient compared with the FP64 one."""
+    import torch
+
+    import inputs
+    import paper_2605_07391_gb300 as mb
+    from paper_2605_07391_gb300 import autograd as ag
+    a = inputs.rmat_transition(20, 16, 3)
+    rp = torch.from_numpy(a.row_ptr).to(dev)
+    col = torch.from_numpy(a.col).to(dev)
+    w = torch.from_numpy(np.random.default_rng(20).standard_normal(a.n_rows))
+    res = {"workload": "rmat20_transition", "nnz": int(a.nnz), "n": int(a.n_rows)}
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(dev)
+        return r, (time.perf_counter() - t0) * 1e3
+
+    A, res["plan_ms"] = timed(lambda: ag.Matrix(rp, col, a.n_rows, a.n_cols, stream=stream))
+    _, res["transpose_and_plan_ms"] = timed(lambda: A.transposed(stream))
+    grads = {}
+    for name, dt, tol, adj_tol in (("f32", torch.float32, 1e-7, 1e-6), ("f64", torch.float64, 1e-12, 1e-12)):
+        vals = torch.from_numpy(a.val).to(dev, dt)
+        wd = w.to(dev, dt)
+        mb.pagerank(A.plan, vals, 0.85, tol=0.0, max_iter=2, stream=stream)          # warm
+        (pi, info), fwd = timed(lambda: mb.pagerank(A.plan, vals, 0.85, tol=tol, max_iter=5000, stream=stream))
+        _, pt = A.transposed()
+
+        def backward():
+            vt = A.transposed_values(vals, stream)
+            lam, ainfo = mb.pagerank_adjoint(A.plan, pt, vt, wd, 0.85, tol=adj_tol, max_iter=5000,
+                                             stream=stream)
+            return mb.sddmm(A.plan, lam, pi, 0.85, stream=stream), ainfo
+        (g, ainfo), bwd = timed(backward)
+        # the same through torch.autograd (what a user calls)
+        v_req = vals.clone().requires_grad_()
+
+        def autograd_step():
+            v_req.grad = None
+            p = ag.pagerank(A, v_req, 0.85, tol=tol, adj_tol=adj_tol)
+            (p * wd).sum().backward()
+            return v_req.grad
+        autograd_step()                      # the autograd engine's first use is not timed
+        _, e2e = timed(autograd_step)
+        grads[name] = g.double()
+        res[name] = {"forward_ms": fwd, "forward_updates": info["iters"], "forward_resid": info["resid"],
+                     "backward_ms": bwd, "adjoint_updates": ainfo["iters"], "adjoint_resid": ainfo["resid"],
+                     "autograd_forward_backward_ms": e2e}
+    res["f32_vs_f64_grad_rel_l1"] = float((grads["f32"] - grads["f64"]).abs().sum() / grads["f64"].abs().sum())
+    A.plan.destroy()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,6 +335,8 @@ def main():
     ap.add_argument("--no-pagerank", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched runs (SpMM and personalised PageRank, R-MAT scale 22)")
+    ap.add_argument("--no-autograd", action="store_true",
+                    help="skip the differentiation run (PageRank value gradient, R-MAT scale 20)")
     ap.add_argument("--batched-k", type=int, nargs="+", default=[8, 32],
                     help="numbers of right-hand sides / seeds of the batched runs")
     ap.add_argument("--no-oracle-check", action="store_true")
@@ -454,6 +514,10 @@ def main():
         # ---- batching: SpMM and personalised PageRank on R-MAT scale 22, k = 8 and 32
         if not args.no_batched:
             out["batched"] = run_batched(args, dev, stream)
+
+        # ---- differentiation: PageRank value gradient by the implicit adjoint, R-MAT scale 20
+        if not args.no_autograd:
+            out["autograd"] = run_autograd(args, dev, stream)
 
         # ---- CPU baseline: the float64 oracle on a bounded sample
         nnz_done, t_used = oracle_sample_rate(a, args.cpu_budget, x64)

@@ -178,6 +178,58 @@ merbit_status merbit_ppr(merbit_plan_t plan, const float* vals, const int32_t* s
                          double alpha, double tol, int max_iter, float* Pi, int* iters_out,
                          double* resid_out, double* resid_hist, void* stream);
 
+/* ---------------------------------------------------------------- differentiation
+ * The backward pass of y = A x needs A^T g and the per-nonzero products g[row] x[col];
+ * the backward pass of the PageRank fixed point needs the adjoint solve below.  None of
+ * these calls has a counterpart in the paper; they reuse its plan and SpMV on A^T.
+ */
+typedef struct merbit_transpose_s* merbit_transpose_t;
+
+/*
+ * merbit_transpose — the CSR of A^T (n_cols x n_rows) from the CSR of A, on the device:
+ * row_ptr_t (n_cols + 1), col_t (nnz; each row of A^T in increasing column order, i.e.
+ * the result does not depend on thread timing) and perm (nnz): A^T's k-th nonzero is A's
+ * nonzero perm[k], so vals_t = vals[perm] (merbit_gather).  Inputs are device arrays,
+ * sorted and duplicate-free per row; the transpose owns its three arrays (read them with
+ * merbit_transpose_get) until merbit_transpose_destroy.  A plan of A^T is
+ * merbit_plan_ex(row_ptr_t, col_t, n_cols, n_rows, nnz, ...); it borrows col_t.
+ * Synchronous.  Errors: EINVAL, EOVERFLOW (sizes beyond int32), ENOMEM, ECUDA.
+ */
+merbit_status merbit_transpose(const int32_t* row_ptr, const int32_t* col_idx, int64_t n_rows,
+                               int64_t n_cols, int64_t nnz, void* stream, merbit_transpose_t* out);
+merbit_status merbit_transpose_get(merbit_transpose_t t, const int32_t** row_ptr_t,
+                                   const int32_t** col_t, const int32_t** perm);
+void merbit_transpose_destroy(merbit_transpose_t t);
+
+/* merbit_gather — dst[i] = src[idx[i]] for i < count; F32 or F64 device arrays. */
+merbit_status merbit_gather(merbit_dtype dtype, const void* src, const int32_t* idx, void* dst,
+                            int64_t count, void* stream);
+
+/*
+ * merbit_sddmm — out[k] = scale * g[row(k)] * x[col(k)] for every nonzero k of the plan's
+ * matrix (the value gradient of y = A x is g[row] x[col]).  g has n_rows entries, x has
+ * n_cols, out has nnz; F32 or F64 device arrays (the plan's column indices must still
+ * be valid).  Asynchronous.  Errors: EINVAL, ECUDA.
+ */
+merbit_status merbit_sddmm(merbit_plan_t plan, merbit_dtype dtype, const void* g, const void* x,
+                           double scale, void* out, void* stream);
+
+/*
+ * merbit_pagerank_adjoint — lambda solving (I - alpha M)^T lambda = w, M = A + (1/n) 1 d^T
+ * the PageRank operator of merbit_pagerank (A = P^T from `plan`, d its dangling
+ * indicator).  For a loss L(pi) at the PageRank fixed point, w = dL/dpi gives
+ * dL/dA_ij = alpha * lambda_i * pi_j (merbit_sddmm with scale alpha, g = lambda, x = pi).
+ * Iterates lambda' = alpha A^T lambda + alpha (sum(lambda)/n) d + w from lambda_0 = w on
+ * `plan_t`, a plan of A^T with values vals_t (F32 or F64, 16-byte aligned), until
+ * ||lambda' - lambda||_1 <= tol * ||w||_1 (tol <= 0: exactly max_iter updates); the
+ * residual reported in resid_out is absolute.  Synchronous.
+ * Errors: EINVAL, ENOTCONV (lambda holds the last iterate), EDEVICE, ENOMEM, ECUDA.
+ */
+merbit_status merbit_pagerank_adjoint(merbit_plan_t plan, merbit_plan_t plan_t, merbit_dtype dtype,
+                                      const void* vals_t, double alpha, const void* w, double tol,
+                                      int max_iter, void* lambda, int* iters_out, double* resid_out,
+                                      void* stream);
+
 /*
  * merbit_spmv_host — y = A x with x and y in HOST memory (pinned or pageable;
  * `vals` stays a device pointer).  x is copied into plan-owned device memory,

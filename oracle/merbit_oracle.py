@@ -11,7 +11,8 @@ counts (Sec. 4.1.1), a literal step-by-step merge-path walk on tiny inputs,
 path invariants, dense brute-force SpMV, closed-form PageRank vectors (n-cycle,
 bidirected star, in-star, 3-chain), closed-form personalised vectors (n-cycle,
 chain ending in a dangling vertex, bidirected star), dense linear solves of both
-fixed-point equations, and numpy's IEEE half conversion for the rounding helper.
+fixed-point equations and of the adjoint equation, central finite differences of
+the PageRank loss and of g^T A x, and numpy's IEEE half conversion for the rounding helper.
 
 Readings of points the paper leaves open (each is also listed in the design
 notes):
@@ -27,6 +28,9 @@ notes):
     it stops when ||pi' - pi||_1 < tol (Sec. 5.5.1 leaves the rule open).
   * Personalised PageRank (the batching extension): one column per seed s, the
     teleport vector is e_s and the dangling mass also returns to s; pi_0 = e_s.
+  * Differentiation (extension): every stored value of P^T is an independent
+    parameter and the dangling set is fixed by the pattern; L = w^T pi gives
+    dL/dA_ij = alpha lambda_i pi_j with (I - alpha M)^T lambda = w.
 """
 from __future__ import annotations
 
@@ -336,6 +340,66 @@ def ppr_dense_solve(dense_pt: np.ndarray, seed: int, alpha: float = 0.85) -> np.
     e[seed] = 1.0
     M = np.eye(n) - alpha * dense_pt - alpha * np.outer(e, d.astype(np.float64))
     return np.linalg.solve(M, (1.0 - alpha) * e)
+
+
+# ---------------------------------------------------------------------------
+# Differentiation (extension): transpose, value gradients, PageRank adjoint
+# ---------------------------------------------------------------------------
+
+def transpose_csr(row_ptr, col, n_cols: int):
+    """CSR of A^T: (row_ptr_t, col_t, perm) with A^T's k-th nonzero = A's nonzero perm[k];
+    each row of A^T lists its columns (A's rows) in increasing order."""
+    col = np.asarray(col, np.int64)
+    perm = np.argsort(col, kind="stable")
+    row_ptr_t = np.zeros(n_cols + 1, np.int64)
+    np.cumsum(np.bincount(col, minlength=n_cols), out=row_ptr_t[1:])
+    return row_ptr_t, _row_ids(row_ptr)[perm], perm
+
+
+def sddmm(row_ptr, col, g, x, scale: float = 1.0) -> np.ndarray:
+    """out[k] = scale * g[row(k)] * x[col(k)]: the value gradient of g^T A x."""
+    rows = _row_ids(row_ptr)
+    return (scale * np.asarray(g, np.float64)[rows]) * np.asarray(x, np.float64)[np.asarray(col, np.int64)]
+
+
+def pagerank_adjoint(row_ptr, col, val, w, alpha: float = 0.85, tol: float = 1e-13,
+                     max_iter: int = 10000) -> dict:
+    """lambda with (I - alpha M)^T lambda = w, M = A + (1/n) 1 d^T the PageRank operator of
+    pagerank_step: iterates lambda' = alpha A^T lambda + alpha (sum(lambda)/n) d + w from
+    lambda_0 = w until ||lambda' - lambda||_1 < tol."""
+    n = np.asarray(row_ptr).size - 1
+    d = dangling_mask(n, col)
+    rt, ct, perm = transpose_csr(row_ptr, col, n)
+    vt = np.asarray(val, np.float64)[perm]
+    w = np.asarray(w, np.float64)
+    lam = w.copy()
+    hist = []
+    for _ in range(max_iter):
+        y, _ = spmv(rt, ct, vt, lam)
+        nxt = alpha * y + w + (alpha * lam.sum() / n) * d
+        hist.append(float(np.abs(nxt - lam).sum()))
+        lam = nxt
+        if hist[-1] < tol:
+            break
+    return {"lambda": lam, "iters": len(hist), "resid": hist}
+
+
+def pagerank_adjoint_dense(dense_pt: np.ndarray, w, alpha: float = 0.85) -> np.ndarray:
+    """Dense solve of (I - alpha M)^T lambda = w (n <= 64)."""
+    dense_pt = np.asarray(dense_pt, np.float64)
+    n = dense_pt.shape[0]
+    d = ~np.any(dense_pt != 0, axis=0)
+    M = dense_pt + (1.0 / n) * np.outer(np.ones(n), d.astype(np.float64))
+    return np.linalg.solve((np.eye(n) - alpha * M).T, np.asarray(w, np.float64))
+
+
+def pagerank_value_gradient(row_ptr, col, val, w, alpha: float = 0.85, tol: float = 1e-13) -> dict:
+    """dL/dval for L = w^T pi at the PageRank fixed point, every stored value of A = P^T
+    taken as an independent parameter (the dangling set fixed by the pattern):
+    dL/dA_ij = alpha lambda_i pi_j with lambda from pagerank_adjoint."""
+    pi = pagerank(row_ptr, col, val, alpha, tol=tol, max_iter=100000)["pi"]
+    lam = pagerank_adjoint(row_ptr, col, val, w, alpha, tol=tol)["lambda"]
+    return {"grad": sddmm(row_ptr, col, lam, pi, alpha), "pi": pi, "lambda": lam}
 
 
 def relative_linf_error(pi, pi_star) -> float:

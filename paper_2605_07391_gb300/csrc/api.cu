@@ -7,7 +7,7 @@
 #include <cstdlib>
 #include <vector>
 
-#include "merbit_internal.cuh"
+#include "extensions.cuh"
 
 namespace merbit {
 cudaError_t build_tiles(const merbit_plan_s* p, const int32_t* row_ptr, cudaStream_t st);
@@ -793,6 +793,93 @@ merbit_status merbit_pagerank_ex(merbit_plan_t p, merbit_dtype dtype, const void
   return pagerank_ir(p, static_cast<const double*>(vals), alpha, tol, max_iter, mode, inner_sweeps,
                      inner_tol, static_cast<double*>(pi), iters_out, resid_out, resid_hist,
                                     launches_out, st);
+}
+
+merbit_status merbit_sddmm(merbit_plan_t p, merbit_dtype dtype, const void* g, const void* x,
+                          double scale, void* out, void* stream) {
+  if (merbit_status s = check_plan(p)) return s;
+  if (dtype != MERBIT_F32 && dtype != MERBIT_F64) return fail(MERBIT_EINVAL, "dtype must be F32 or F64");
+  if (p->nnz == 0) return MERBIT_OK;
+  if (!g || !x || !out) return fail(MERBIT_EINVAL, "g, x or out is NULL");
+  MB_TRY(sddmm(p, dtype, g, x, scale, out, as_stream(stream)));
+  return MERBIT_OK;
+}
+
+merbit_status merbit_pagerank_adjoint(merbit_plan_t p, merbit_plan_t pt, merbit_dtype dtype,
+                                      const void* vals_t, double alpha, const void* w, double tol,
+                                      int max_iter, void* lambda, int* iters_out,
+                                      double* resid_out, void* stream) {
+  if (merbit_status s = check_plan(p)) return s;
+  if (merbit_status s = check_plan(pt)) return s;
+  if (p->n_rows != p->n_cols) return fail(MERBIT_EINVAL, "PageRank needs a square plan");
+  if (pt->n_rows != p->n_cols || pt->n_cols != p->n_rows || pt->nnz != p->nnz)
+    return fail(MERBIT_EINVAL, "plan_t is not a plan of the transposed matrix");
+  if (dtype != MERBIT_F32 && dtype != MERBIT_F64) return fail(MERBIT_EINVAL, "dtype must be F32 or F64");
+  if (!(alpha >= 0.0 && alpha < 1.0)) return fail(MERBIT_EINVAL, "alpha must be in [0, 1)");
+  if (max_iter < 1) return fail(MERBIT_EINVAL, "max_iter must be >= 1");
+  const int64_t n = p->n_rows;
+  if (n == 0) {
+    if (iters_out) *iters_out = 0;
+    if (resid_out) *resid_out = 0.0;
+    return MERBIT_OK;
+  }
+  if (!w || !lambda) return fail(MERBIT_EINVAL, "w or lambda is NULL");
+  if (pt->nnz > 0 && (!vals_t || !aligned(vals_t, 16)))
+    return fail(MERBIT_EINVAL, "vals_t must be a 16-byte aligned device array");
+  cudaStream_t st = as_stream(stream);
+  if (merbit_status s = ensure_dangling(p, st)) return s;
+  if (merbit_status s = ensure_hist(pt, (size_t)max_iter)) return s;
+  const size_t es = dtype_size(dtype);
+  MB_TRY(grow(&pt->scratch, &pt->scratch_bytes, align256(es * (size_t)n) + 256));
+  void* buf[2] = {lambda, pt->scratch};
+  double* wnorm = reinterpret_cast<double*>(static_cast<char*>(pt->scratch) + align256(es * (size_t)n));
+  // lambda_0 = w, S_0 = sum(w); state cleared
+  MB_TRY(cudaMemcpyAsync(lambda, w, es * (size_t)n, cudaMemcpyDeviceToDevice, st));
+  pr_state_init_kernel<<<1, 1, 0, st>>>(pt->hist, 0.0, pt->red);
+  MB_TRY(cudaGetLastError());
+  MB_TRY(vec_sum(w, dtype, n, pt->hist + 1, false, pt->num_sms, st));
+  MB_TRY(vec_sum(w, dtype, n, wnorm, true, pt->num_sms, st));
+  const int kBatch = 8;
+  int k = 0;
+  StateWord sw{};
+  while (k < max_iter) {
+    const int stop = std::min(max_iter, k + kBatch);
+    for (; k < stop; ++k) {
+      AdjParams prm;
+      prm.out = buf[(k + 1) & 1];
+      prm.w = w;
+      prm.dang = p->dangling_bits;
+      prm.alpha = alpha;
+      prm.inv_n = 1.0 / (double)n;
+      prm.tol = tol;
+      prm.wnorm = wnorm;
+      prm.s_in = pt->hist + 2 * k + 1;
+      prm.s_out = pt->hist + 2 * (k + 1);
+      prm.iter = k;
+      cudaError_t e = dtype == MERBIT_F32
+          ? spmv_adj_f32(pt, static_cast<const float*>(vals_t), static_cast<const float*>(buf[k & 1]), prm, st)
+          : spmv_adj_f64(pt, static_cast<const double*>(vals_t), static_cast<const double*>(buf[k & 1]), prm, st);
+      if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    }
+    MB_TRY(read_state(pt, st, &sw));
+    if (sw.err || sw.done) break;
+  }
+  if (sw.err) {
+    MB_TRY(reset_device_state(pt, st));
+    MB_TRY(cudaStreamSynchronize(st));
+    return fail(MERBIT_EDEVICE, "a kernel reported error bits 0x%x", sw.err);
+  }
+  const int iters = sw.done ? sw.iters : max_iter;
+  if (iters & 1) MB_TRY(cudaMemcpyAsync(lambda, buf[1], es * (size_t)n, cudaMemcpyDeviceToDevice, st));
+  double last = 0.0;
+  MB_TRY(cudaMemcpyAsync(&last, pt->hist + 2 * (size_t)iters, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MB_TRY(cudaStreamSynchronize(st));
+  if (iters_out) *iters_out = iters;
+  if (resid_out) *resid_out = last;
+  if (tol > 0 && !sw.done)
+    return fail(MERBIT_ENOTCONV, "adjoint solve did not reach tol %.3g * ||w||_1 in %d updates (residual %.3g)",
+                tol, max_iter, last);
+  return MERBIT_OK;
 }
 
 merbit_status merbit_pagerank(merbit_plan_t p, merbit_dtype dtype, const void* vals, double alpha,

@@ -28,7 +28,8 @@ EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_
            "merbit_plan_sync", "merbit_plan_export", "merbit_spmv", "merbit_spmv_ex", "merbit_spmm",
            "merbit_ppr", "merbit_spmv_host",
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
-           "merbit_last_error", "merbit_version"]
+           "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
+           "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_last_error", "merbit_version"]
 
 
 class MerbitError(RuntimeError):
@@ -83,6 +84,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_pagerank_ex": [vp, i32, vp, dbl, dbl, i32, i32, i32, dbl, vp,
                                    ctypes.POINTER(i32), ctypes.POINTER(dbl), vp,
                                    ctypes.POINTER(i32), vp],
+            "merbit_transpose": [vp, vp, i64, i64, i64, vp, ctypes.POINTER(vp)],
+            "merbit_transpose_get": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)],
+            "merbit_gather": [i32, vp, vp, vp, i64, vp],
+            "merbit_sddmm": [vp, i32, vp, vp, dbl, vp, vp],
+            "merbit_pagerank_adjoint": [vp, vp, i32, vp, dbl, vp, dbl, i32, vp, ctypes.POINTER(i32),
+                                        ctypes.POINTER(dbl), vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -90,6 +97,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             f.restype = i32
         lib.merbit_plan_destroy.argtypes = [vp]
         lib.merbit_plan_destroy.restype = None
+        lib.merbit_transpose_destroy.argtypes = [vp]
+        lib.merbit_transpose_destroy.restype = None
         lib.merbit_last_error.restype = ctypes.c_char_p
         lib.merbit_version.restype = ctypes.c_char_p
         _lib = lib
@@ -196,6 +205,105 @@ class Plan:
             self.destroy()
         except Exception:
             pass
+
+
+class _DeviceArray:
+    """A library-owned device array seen by torch through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+        self._owner = owner
+
+
+class Transpose:
+    """merbit_transpose: the CSR of A^T on the device (row_ptr_t, col_t, perm), owned by
+    the library; the tensors below are views that keep this object alive."""
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, n_rows: int | None = None,
+                 n_cols: int | None = None, stream=None):
+        lib = load()
+        _need_cuda(row_ptr, col_idx)
+        if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32:
+            raise ValueError("row_ptr and col_idx must be int32")
+        n_rows = row_ptr.numel() - 1 if n_rows is None else n_rows
+        n_cols = n_rows if n_cols is None else n_cols
+        self._handle = ctypes.c_void_p()
+        _check("merbit_transpose", lib.merbit_transpose(_ptr(row_ptr), _ptr(col_idx), n_rows, n_cols,
+                                                       col_idx.numel(), _stream(stream),
+                                                       ctypes.byref(self._handle)))
+        rp, ct, pm = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check("merbit_transpose_get", lib.merbit_transpose_get(self._handle, ctypes.byref(rp),
+                                                               ctypes.byref(ct), ctypes.byref(pm)))
+        nnz = col_idx.numel()
+        dev = row_ptr.device
+        self.row_ptr_t = torch.as_tensor(_DeviceArray(rp.value, n_cols + 1, "<i4", self), device=dev)
+        self.col_t = torch.as_tensor(_DeviceArray(ct.value, nnz, "<i4", self), device=dev)
+        self.perm = torch.as_tensor(_DeviceArray(pm.value, nnz, "<i4", self), device=dev)
+        self.n_rows, self.n_cols, self.nnz = n_cols, n_rows, nnz    # of A^T
+
+    def plan(self, sigma: int = 14, stream=None) -> "Plan":
+        """A plan of A^T (borrows col_t)."""
+        return Plan(self.row_ptr_t, self.col_t, self.n_rows, self.n_cols, sigma=sigma, stream=stream)
+
+    def destroy(self):
+        if getattr(self, "_handle", None):
+            load().merbit_transpose_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def transpose(row_ptr, col_idx, n_rows=None, n_cols=None, stream=None) -> Transpose:
+    return Transpose(row_ptr, col_idx, n_rows, n_cols, stream)
+
+
+def gather(src: torch.Tensor, idx: torch.Tensor, out: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    """merbit_gather: out[i] = src[idx[i]] (f32 or f64, idx int32)."""
+    _need_cuda(src, idx, out)
+    if idx.dtype != torch.int32:
+        raise ValueError("idx must be int32")
+    if out is None:
+        out = torch.empty(idx.numel(), dtype=src.dtype, device=src.device)
+    _check("merbit_gather", load().merbit_gather(_dt(src), _ptr(src), _ptr(idx), _ptr(out), idx.numel(),
+                                                _stream(stream)))
+    return out
+
+
+def sddmm(p: "Plan", g: torch.Tensor, x: torch.Tensor, scale: float = 1.0,
+          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """merbit_sddmm: out[k] = scale * g[row(k)] * x[col(k)] over the plan's nonzeros."""
+    _need_cuda(g, x, out)
+    if g.dtype != x.dtype:
+        raise ValueError("g and x must have the same dtype")
+    if out is None:
+        out = torch.empty(p.nnz, dtype=g.dtype, device=g.device)
+    _check("merbit_sddmm", load().merbit_sddmm(p.handle, _dt(g), _ptr(g), _ptr(x), scale, _ptr(out),
+                                              _stream(stream)))
+    return out
+
+
+def pagerank_adjoint(p: "Plan", pt: "Plan", vals_t: torch.Tensor, w: torch.Tensor,
+                     alpha: float = 0.85, tol: float = 1e-12, max_iter: int = 10000,
+                     lam: torch.Tensor | None = None, stream=None) -> tuple[torch.Tensor, dict]:
+    """merbit_pagerank_adjoint: lambda with (I - alpha M)^T lambda = w; stops at
+    ||lambda' - lambda||_1 <= tol * ||w||_1.  Returns (lambda, {iters, resid, converged})."""
+    _need_cuda(vals_t, w, lam)
+    if vals_t.dtype != w.dtype:
+        raise ValueError("vals_t and w must have the same dtype")
+    if lam is None:
+        lam = torch.empty_like(w)
+    iters = ctypes.c_int(0)
+    resid = ctypes.c_double(0.0)
+    st = _check("merbit_pagerank_adjoint", load().merbit_pagerank_adjoint(
+        p.handle, pt.handle, _dt(vals_t), _ptr(vals_t), alpha, _ptr(w), tol, max_iter, _ptr(lam),
+        ctypes.byref(iters), ctypes.byref(resid), _stream(stream)), allow=(5,))
+    return lam, {"iters": iters.value, "resid": resid.value, "converged": st == 0}
 
 
 def plan(row_ptr, col_idx, n_rows=None, n_cols=None, sigma=14, stream=None) -> Plan:

@@ -403,6 +403,92 @@ def test_ppr_invariants_rmat14():
                                       - Pi).sum(axis=0), rtol=1e-14)
 
 
+# Differentiation: transpose, value gradients, PageRank adjoint
+
+def _dense_of(a):
+    dense = np.zeros((a.n_rows, a.n_cols))
+    for r in range(a.n_rows):
+        dense[r, a.col[a.row_ptr[r]:a.row_ptr[r + 1]]] = a.val[a.row_ptr[r]:a.row_ptr[r + 1]]
+    return dense
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_transpose_matches_dense(seed):
+    a = inputs.random_sparse(40 + 7 * seed, 23 + 11 * seed, 0.15, seed, empty_frac=0.2)
+    rt, ct, perm = oracle.transpose_csr(a.row_ptr, a.col, a.n_cols)
+    t = inputs.CSR(a.n_cols, a.n_rows, rt.astype(np.int32), ct.astype(np.int32), a.val[perm], "t")
+    np.testing.assert_array_equal(_dense_of(t), _dense_of(a).T)
+    for r in range(t.n_rows):
+        assert np.all(np.diff(ct[rt[r]:rt[r + 1]]) > 0)
+
+
+def test_sddmm_is_the_gradient_of_the_bilinear_form():
+    """d(g^T A x)/d val_k = g[row_k] x[col_k] (central differences, exact for a linear form),
+    and d(g^T A x)/dx = A^T g."""
+    a = inputs.random_sparse(30, 20, 0.2, 4)
+    rng = np.random.default_rng(1)
+    g, x = rng.standard_normal(a.n_rows), rng.standard_normal(a.n_cols)
+
+    def L(v, xx):
+        return float(g @ oracle.spmv(a.row_ptr, a.col, v, xx)[0])
+    grad = oracle.sddmm(a.row_ptr, a.col, g, x)
+    h = 1e-3
+    for k in range(a.nnz):
+        e = np.zeros(a.nnz)
+        e[k] = h
+        fd = (L(a.val + e, x) - L(a.val - e, x)) / (2 * h)
+        assert abs(fd - grad[k]) < 1e-10
+    np.testing.assert_allclose(oracle.sddmm(a.row_ptr, a.col, g, x, 0.5), 0.5 * grad, rtol=1e-15)
+    rt, ct, perm = oracle.transpose_csr(a.row_ptr, a.col, a.n_cols)
+    gx = oracle.spmv(rt, ct, a.val[perm], g)[0]
+    np.testing.assert_allclose(gx, _dense_of(a).T @ g, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pagerank_adjoint_matches_dense_solve(seed):
+    a = inputs.random_graph_transition(25 + 9 * seed, 0.08, seed)
+    w = np.random.default_rng(seed).standard_normal(a.n_rows)
+    lam = oracle.pagerank_adjoint(a.row_ptr, a.col, a.val, w, ALPHA, tol=1e-14)["lambda"]
+    np.testing.assert_allclose(lam, oracle.pagerank_adjoint_dense(_dense_of(a), w, ALPHA),
+                               rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_pagerank_gradient_central_differences(seed):
+    """L(val) = w^T pi(val): every value's central difference (h = 1e-6) against
+    alpha lambda[row] pi[col]; the graph has dangling vertices."""
+    a = inputs.random_graph_transition(18 + 5 * seed, 0.12, 10 + seed)
+    assert oracle.dangling_mask(a.n_rows, a.col).any()
+    w = np.random.default_rng(seed).standard_normal(a.n_rows)
+    grad = oracle.pagerank_value_gradient(a.row_ptr, a.col, a.val, w, ALPHA)["grad"]
+
+    def L(v):
+        return float(w @ oracle.pagerank(a.row_ptr, a.col, v, ALPHA, tol=1e-15, max_iter=100000)["pi"])
+    h = 1e-6
+    for k in range(a.nnz):
+        e = np.zeros(a.nnz)
+        e[k] = h
+        fd = (L(a.val + e) - L(a.val - e)) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-6 * max(1.0, abs(grad[k])) * 10, (k, fd, grad[k])
+
+
+def test_pagerank_gradient_central_differences_rmat():
+    """The differentiation workload's check in small: 64 random values of an R-MAT
+    transition matrix, central differences with step 1e-3 in FP64."""
+    a = inputs.rmat_transition(10, 16, 2)
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal(a.n_rows)
+    grad = oracle.pagerank_value_gradient(a.row_ptr, a.col, a.val, w, ALPHA)["grad"]
+    h = 1e-3
+    for k in rng.choice(a.nnz, 64, replace=False):
+        e = np.zeros(a.nnz)
+        e[k] = h
+        lp = float(w @ oracle.pagerank(a.row_ptr, a.col, a.val + e, ALPHA, tol=1e-15, max_iter=100000)["pi"])
+        lm = float(w @ oracle.pagerank(a.row_ptr, a.col, a.val - e, ALPHA, tol=1e-15, max_iter=100000)["pi"])
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-4 * abs(grad[k]) + 1e-9, (k, fd, grad[k])
+
+
 def test_relative_linf_error():
     assert oracle.relative_linf_error([1.0, 2.2], [1.0, 2.0]) == pytest.approx(0.1)
 
