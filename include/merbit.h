@@ -231,6 +231,60 @@ merbit_status merbit_pagerank_adjoint(merbit_plan_t plan, merbit_plan_t plan_t, 
                                       void* stream);
 
 /*
+ * merbit_autotune_sigma — picks the plan's steps per lane (sigma, Sec. 4.1.1) for one
+ * matrix and value type by measurement: for each of the `count` candidates (each in
+ * [1, 14]) it builds a plan, runs one warm-up SpMV and `reps` timed ones (CUDA events on
+ * `stream`, x = 0) and frees the plan.  best_sigma = the fastest candidate; ms_out (HOST,
+ * count entries, may be NULL) = mean milliseconds per product.  CSR arrays and vals are
+ * device pointers as in merbit_plan_ex / merbit_spmv_ex; dtype F32 or F64.  Synchronous.
+ * Errors: EINVAL, ENOMEM, ECUDA, and those of merbit_plan_ex / merbit_spmv_ex.
+ */
+merbit_status merbit_autotune_sigma(const int32_t* row_ptr, const int32_t* col_idx, int64_t n_rows,
+                                    int64_t n_cols, int64_t nnz, merbit_dtype dtype, const void* vals,
+                                    const int* candidates, int count, int reps, void* stream,
+                                    int* best_sigma, float* ms_out);
+
+/* ---------------------------------------------------------------- many graphs
+ * PageRank of many independent graphs in one CUDA-graph launch (the batching extension;
+ * no counterpart in the paper).  The graphs are the diagonal blocks of one block-diagonal
+ * CSR matrix (the transition matrices P^T of each graph, vertex ids offset by
+ * graph_offsets), so one MERBIT plan balances the work across all of them.
+ */
+typedef struct merbit_batch_s* merbit_batch_t;
+
+/*
+ * merbit_batch_plan — plan of the block-diagonal matrix (n x n, nnz nonzeros, device
+ * CSR; the batch borrows col_idx).  graph_offsets (HOST, num_graphs + 1 entries) gives
+ * graph g the vertices [graph_offsets[g], graph_offsets[g+1]); every graph has at least
+ * one vertex and every nonzero must stay inside its graph's diagonal block (checked:
+ * EINVAL otherwise).  sigma as in merbit_plan_ex.  Synchronous.  Errors: EINVAL,
+ * EOVERFLOW, ENOMEM, ECUDA.
+ */
+merbit_status merbit_batch_plan(const int32_t* row_ptr, const int32_t* col_idx, int64_t n,
+                                int64_t nnz, const int64_t* graph_offsets, int num_graphs,
+                                int sigma, void* stream, merbit_batch_t* out);
+
+/*
+ * merbit_batch_pagerank — for every graph, the PageRank power iteration of
+ * merbit_pagerank (pi_0 = 1/n_g, teleport and dangling mass spread over the graph's own
+ * vertices) until its ||pi' - pi||_1 < tol, all graphs advancing together one round per
+ * SpMV over the whole matrix; a converged graph is left untouched by later rounds.  The
+ * whole solve is one CUDA-graph launch with a device-side loop (recorded on first use and
+ * kept while dtype, vals, pi, alpha, tol and max_iter stay the same).  vals: F32 or F64
+ * device values (16-byte aligned); pi: n entries of that type (graph g's vector in its
+ * vertex range).  iters (HOST, num_graphs or NULL): updates of each graph; resid (HOST,
+ * num_graphs or NULL): each graph's last ||pi' - pi||_1; rounds_out: rounds run.
+ * Synchronous.  Errors: EINVAL, ENOTCONV (some graph did not reach tol in max_iter rounds;
+ * pi holds every graph's last iterate), EDEVICE, ENOMEM, ECUDA.
+ */
+merbit_status merbit_batch_pagerank(merbit_batch_t batch, merbit_dtype dtype, const void* vals,
+                                    double alpha, double tol, int max_iter, void* pi, int* iters,
+                                    double* resid, int* rounds_out, void* stream);
+/* The plan of the block-diagonal matrix (owned by the batch). */
+merbit_plan_t merbit_batch_get_plan(merbit_batch_t batch);
+void merbit_batch_destroy(merbit_batch_t batch);
+
+/*
  * merbit_spmv_host — y = A x with x and y in HOST memory (pinned or pageable;
  * `vals` stays a device pointer).  x is copied into plan-owned device memory,
  * the product runs on `stream`, y is copied back, and the stream is

@@ -130,6 +130,51 @@ def rmat_transition(scale: int, edge_factor: int = 16, seed: int = 1) -> CSR:
                {"scale": scale, "edge_factor": edge_factor, "seed": seed})
 
 
+def block_diagonal(parts: list) -> tuple[CSR, np.ndarray]:
+    """Square CSR matrices as the diagonal blocks of one CSR; returns (CSR, offsets) with
+    offsets[g] the first row / column of block g (int64, len(parts) + 1)."""
+    sizes = np.array([p.n_rows for p in parts], np.int64)
+    nnzs = np.array([p.nnz for p in parts], np.int64)
+    off = np.zeros(len(parts) + 1, np.int64)
+    np.cumsum(sizes, out=off[1:])
+    zoff = np.zeros(len(parts) + 1, np.int64)
+    np.cumsum(nnzs, out=zoff[1:])
+    n, nnz = int(off[-1]), int(zoff[-1])
+    if n + nnz >= 2**31:
+        raise ValueError("batch too large for int32 indices")
+    row_ptr = np.empty(n + 1, np.int32)
+    col = np.empty(nnz, np.int32)
+    val = np.empty(nnz, np.float64)
+    for g, p in enumerate(parts):
+        assert p.n_rows == p.n_cols
+        row_ptr[off[g]:off[g + 1]] = p.row_ptr[:-1] + zoff[g]
+        col[zoff[g]:zoff[g + 1]] = p.col + off[g]
+        val[zoff[g]:zoff[g + 1]] = p.val
+    row_ptr[n] = nnz
+    return CSR(n, n, row_ptr, col, val, f"blockdiag{len(parts)}"), off
+
+
+def rmat_batch(num_graphs: int, seed: int, scales: tuple[int, int] = (10, 20),
+               edge_factors: tuple[int, int] = (8, 32), threads: int = 8):
+    """Many independent R-MAT transition matrices as the diagonal blocks of one CSR.
+
+    Graph g has scale s_g and edge factor f_g drawn uniformly from the inclusive integer
+    ranges (vertex counts log-uniform over powers of two) and its own generator seed.
+    Returns (CSR, offsets) with offsets[g] the first vertex of graph g (int64, G + 1)."""
+    import concurrent.futures as cf
+    rng = np.random.default_rng(seed)
+    sc = rng.integers(scales[0], scales[1] + 1, num_graphs)
+    ef = rng.integers(edge_factors[0], edge_factors[1] + 1, num_graphs)
+    seeds = rng.integers(1, 2**31 - 1, num_graphs)
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda g: rmat_transition(int(sc[g]), int(ef[g]), int(seeds[g])),
+                            range(num_graphs)))
+    csr, off = block_diagonal(parts)
+    csr.name = f"rmat_batch{num_graphs}_s{seed}"
+    csr.meta = {"scales": sc.tolist(), "edge_factors": ef.tolist()}
+    return csr, off
+
+
 def uniform_open0(n: int, seed: int, stream: int = 21) -> np.ndarray:
     """float64 values in (0, 1]."""
     out = np.empty(n, np.float64)

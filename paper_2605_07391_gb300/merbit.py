@@ -29,7 +29,9 @@ EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_
            "merbit_ppr", "merbit_spmv_host",
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
            "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
-           "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_last_error", "merbit_version"]
+           "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
+           "merbit_batch_get_plan", "merbit_batch_destroy", "merbit_autotune_sigma", "merbit_last_error",
+           "merbit_version"]
 
 
 class MerbitError(RuntimeError):
@@ -90,6 +92,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_sddmm": [vp, i32, vp, vp, dbl, vp, vp],
             "merbit_pagerank_adjoint": [vp, vp, i32, vp, dbl, vp, dbl, i32, vp, ctypes.POINTER(i32),
                                         ctypes.POINTER(dbl), vp],
+            "merbit_batch_plan": [vp, vp, i64, i64, vp, i32, i32, vp, ctypes.POINTER(vp)],
+            "merbit_batch_pagerank": [vp, i32, vp, dbl, dbl, i32, vp, vp, vp, ctypes.POINTER(i32), vp],
+            "merbit_autotune_sigma": [vp, vp, i64, i64, i64, i32, vp, vp, i32, i32, vp,
+                                      ctypes.POINTER(i32), vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -99,6 +105,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.merbit_plan_destroy.restype = None
         lib.merbit_transpose_destroy.argtypes = [vp]
         lib.merbit_transpose_destroy.restype = None
+        lib.merbit_batch_destroy.argtypes = [vp]
+        lib.merbit_batch_destroy.restype = None
+        lib.merbit_batch_get_plan.argtypes = [vp]
+        lib.merbit_batch_get_plan.restype = vp
         lib.merbit_last_error.restype = ctypes.c_char_p
         lib.merbit_version.restype = ctypes.c_char_p
         _lib = lib
@@ -256,6 +266,77 @@ class Transpose:
             self.destroy()
         except Exception:
             pass
+
+
+class Batch:
+    """merbit_batch_plan: many graphs as the diagonal blocks of one CSR (graph g owns the
+    vertices [offsets[g], offsets[g+1])); borrows col_idx."""
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, offsets, sigma: int = 14,
+                 stream=None):
+        lib = load()
+        _need_cuda(row_ptr, col_idx)
+        if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32:
+            raise ValueError("row_ptr and col_idx must be int32")
+        self._offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self.num_graphs = self._offsets.size - 1
+        self.n = row_ptr.numel() - 1
+        self._col = col_idx
+        self._handle = ctypes.c_void_p()
+        _check("merbit_batch_plan", lib.merbit_batch_plan(
+            _ptr(row_ptr), _ptr(col_idx), self.n, col_idx.numel(),
+            self._offsets.ctypes.data_as(ctypes.c_void_p), self.num_graphs, sigma, _stream(stream),
+            ctypes.byref(self._handle)))
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._handle:
+            raise MerbitError("batch", 1, "batch was destroyed")
+        return self._handle
+
+    def pagerank(self, vals: torch.Tensor, alpha: float = 0.85, tol: float = 1e-8,
+                 max_iter: int = 1000, pi: torch.Tensor | None = None, stream=None):
+        """merbit_batch_pagerank.  Returns (pi, info) with per-graph iters and resid."""
+        _need_cuda(vals, pi)
+        if pi is None:
+            pi = torch.empty(self.n, dtype=vals.dtype, device=vals.device)
+        iters = np.zeros(self.num_graphs, np.int32)
+        resid = np.zeros(self.num_graphs, np.float64)
+        rounds = ctypes.c_int(0)
+        st = _check("merbit_batch_pagerank", load().merbit_batch_pagerank(
+            self.handle, _dt(vals), _ptr(vals), alpha, tol, max_iter, _ptr(pi),
+            iters.ctypes.data_as(ctypes.c_void_p), resid.ctypes.data_as(ctypes.c_void_p),
+            ctypes.byref(rounds), _stream(stream)), allow=(5,))
+        return pi, {"iters": iters, "resid": resid, "rounds": rounds.value, "converged": st == 0}
+
+    def destroy(self):
+        if getattr(self, "_handle", None):
+            load().merbit_batch_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def autotune_sigma(row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor,
+                   n_rows: int | None = None, n_cols: int | None = None,
+                   candidates=(14, 12, 10, 8, 7), reps: int = 5, stream=None) -> tuple[int, dict]:
+    """merbit_autotune_sigma: the fastest steps-per-lane for this matrix and value type.
+    Returns (best sigma, {sigma: ms per SpMV})."""
+    _need_cuda(row_ptr, col_idx, vals)
+    n_rows = row_ptr.numel() - 1 if n_rows is None else n_rows
+    n_cols = n_rows if n_cols is None else n_cols
+    cand = np.ascontiguousarray(np.asarray(candidates, dtype=np.int32))
+    ms = np.zeros(cand.size, np.float32)
+    best = ctypes.c_int(0)
+    _check("merbit_autotune_sigma", load().merbit_autotune_sigma(
+        _ptr(row_ptr), _ptr(col_idx), n_rows, n_cols, col_idx.numel(), _dt(vals), _ptr(vals),
+        cand.ctypes.data_as(ctypes.c_void_p), cand.size, reps, _stream(stream), ctypes.byref(best),
+        ms.ctypes.data_as(ctypes.c_void_p)))
+    return best.value, {int(c): float(t) for c, t in zip(cand, ms)}
 
 
 def transpose(row_ptr, col_idx, n_rows=None, n_cols=None, stream=None) -> Transpose:

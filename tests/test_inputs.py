@@ -45,3 +45,29 @@ def test_vectors():
     assert np.all((x >= 0) & (x < 1)) and np.array_equal(x, inputs.uniform_vector(1000, 2))
     u = inputs.uniform_open0(1000, 2)
     assert np.all((u > 0) & (u <= 1))
+
+
+def test_rmat_batch_is_block_diagonal():
+    a, off = inputs.rmat_batch(6, 3, scales=(4, 9), edge_factors=(4, 12), threads=3)
+    a.check()
+    assert off[0] == 0 and off[-1] == a.n_rows and np.all(np.diff(off) > 0)
+    sc, ef = a.meta["scales"], a.meta["edge_factors"]
+    assert all(4 <= s <= 9 for s in sc) and all(4 <= f <= 12 for f in ef)
+    rows = np.repeat(np.arange(a.n_rows), np.diff(a.row_ptr))
+    g_row = np.searchsorted(off, rows, side="right") - 1
+    g_col = np.searchsorted(off, a.col, side="right") - 1
+    assert np.array_equal(g_row, g_col)
+    for g in range(6):
+        assert off[g + 1] - off[g] == 1 << sc[g]
+    b, off2 = inputs.rmat_batch(6, 3, scales=(4, 9), edge_factors=(4, 12), threads=1)
+    assert np.array_equal(b.col, a.col) and np.array_equal(b.val, a.val) and np.array_equal(off, off2)
+
+
+def test_block_diagonal_of_small_graphs():
+    parts = [inputs.cycle_graph(3), inputs.in_star(2), inputs.cycle_graph(1)]
+    a, off = inputs.block_diagonal(parts)
+    assert off.tolist() == [0, 3, 6, 7]
+    dense = np.zeros((7, 7))
+    for r in range(7):
+        dense[r, a.col[a.row_ptr[r]:a.row_ptr[r + 1]]] = a.val[a.row_ptr[r]:a.row_ptr[r + 1]]
+    assert dense[1, 0] == 1.0 and dense[3, 4] == 1.0 and dense[6, 6] == 1.0
