@@ -5,11 +5,11 @@
 // over the concatenated rows and nonzeros balances the work across graph boundaries
 // exactly as it does across rows of one graph.  Per round, the SpMV kernel runs once
 // over the whole matrix with an epilogue that knows each row's graph: it applies that
-// graph's teleport and dangling term, leaves graphs that have converged untouched, and
-// adds per-graph partial residuals and dangling masses (per-thread sums, flushed to
-// per-graph FP64 accumulators when a thread's rows change graph).  A one-block check
-// kernel then closes the round: per graph, the residual against tol, the next dangling
-// mass, and the stop of the device-side while loop when no graph is left.
+// graph's teleport and dangling term and leaves graphs that have converged untouched.
+// A streaming pass over contiguous row ranges then forms each graph's residual
+// ||pi' - pi||_1 and dangling mass (warp sums, one FP64 atomic per warp and graph), and a
+// one-block check kernel closes the round: per graph, the residual against tol, the next
+// dangling mass, and the stop of the device-side while loop when no graph is left.
 //
 // The solve is one cudaGraphLaunch: initialisation, a conditional while node whose
 // body is two rounds (x -> y, then y -> x, so kernel arguments stay fixed), and a
@@ -56,8 +56,6 @@ struct BatchParams {
   const double* inv_n;       // 1 / n_g
   const double* D;           // dangling mass of each graph's current iterate
   const int* conv;           // updates at convergence, -1 while active
-  double* acc;               // [2G]: sum |pi' - pi|, dangling mass of pi'
-  const uint32_t* dang;      // dangling bits of the whole matrix
   double alpha;
 };
 
@@ -66,12 +64,10 @@ struct EpiBatchPR {
   static constexpr bool kReduce = false;
   BatchParams p;
   T* out;
-  const T* xold;
-  mutable int gid, lo, hi;
+  mutable int lo, hi;
   mutable bool frozen;
   mutable T a, tele;
   __device__ __forceinline__ void init() {
-    gid = -1;
     lo = hi = 0;
     frozen = true;
     a = static_cast<T>(p.alpha);
@@ -80,37 +76,80 @@ struct EpiBatchPR {
   __device__ __forceinline__ bool skip(const RedState* red) const {
     return *reinterpret_cast<const volatile int*>(&red->done) != 0;
   }
-  __device__ __forceinline__ void flush(double& p0, double& p1) const {
-    if (gid >= 0 && !frozen && (p0 != 0.0 || p1 != 0.0)) {
-      atomicAdd(p.acc + 2 * gid, p0);
-      atomicAdd(p.acc + 2 * gid + 1, p1);
-    }
-    p0 = p1 = 0.0;
-  }
-  __device__ __forceinline__ void locate(int r, double& p0, double& p1) const {
+  __device__ __forceinline__ void locate(int r) const {
     if (r >= lo && r < hi) return;
-    flush(p0, p1);
-    gid = graph_of(p.off, p.G, r);
+    const int gid = graph_of(p.off, p.G, r);
     lo = __ldg(p.off + gid);
     hi = __ldg(p.off + gid + 1);
     frozen = __ldg(p.conv + gid) >= 0;
     tele = static_cast<T>((p.alpha * __ldg(p.D + gid) + 1.0 - p.alpha) * __ldg(p.inv_n + gid));
   }
-  __device__ __forceinline__ void put(int r, T v, double& p0, double& p1) const {
-    out[r] = v;
-    p0 += fabs(static_cast<double>(v) - static_cast<double>(xold[r]));
-    if (is_dangling(p.dang, r)) p1 += static_cast<double>(v);
+  __device__ __forceinline__ void row(int r, T s, double&, double&) const {
+    locate(r);
+    if (!frozen) out[r] = a * s + tele;
   }
-  __device__ __forceinline__ void row(int r, T s, double& p0, double& p1) const {
-    locate(r, p0, p1);
-    if (!frozen) put(r, a * s + tele, p0, p1);
-  }
-  __device__ __forceinline__ void row64(int r, double s, double& p0, double& p1) const {
-    locate(r, p0, p1);
-    if (!frozen) put(r, static_cast<T>(p.alpha * s + static_cast<double>(tele)), p0, p1);
+  __device__ __forceinline__ void row64(int r, double s, double&, double&) const {
+    locate(r);
+    if (!frozen) out[r] = static_cast<T>(p.alpha * s + static_cast<double>(tele));
   }
   __device__ __forceinline__ void finish(double, double, RedState*) const {}
 };
+
+constexpr int kRowsPerWarp = 2048;
+
+// acc[2g] += sum |y - x|, acc[2g + 1] += sum of y over dangling rows, for active graphs.
+// A warp takes kRowsPerWarp consecutive rows, its lanes consecutive rows within them; a
+// lane flushes its partial sums only when its rows enter another graph, and at the end
+// the warp adds the lanes of each graph together before one atomic per graph.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    batch_reduce_kernel(const T* __restrict__ y, const T* __restrict__ x, const int32_t* off,
+                        int G, const int* conv, const uint32_t* dang, double* acc,
+                        const RedState* red, int64_t n) {
+  if (*reinterpret_cast<const volatile int*>(&red->done)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c * kRowsPerWarp < n;
+       c += warps) {
+    const int64_t r_end = (c + 1) * kRowsPerWarp < n ? (c + 1) * kRowsPerWarp : n;
+    int gid = -1, lo = 0, hi = 0;
+    bool live = false;
+    double p0 = 0.0, p1 = 0.0;
+    for (int64_t r = c * kRowsPerWarp + lane; r < r_end; r += 32) {
+      if (r < lo || r >= hi) {
+        if (live && (p0 != 0.0 || p1 != 0.0)) {
+          atomicAdd(acc + 2 * gid, p0);
+          atomicAdd(acc + 2 * gid + 1, p1);
+        }
+        p0 = p1 = 0.0;
+        gid = graph_of(off, G, (int)r);
+        lo = off[gid];
+        hi = off[gid + 1];
+        live = conv[gid] < 0;
+      }
+      if (!live) continue;
+      const T v = y[r];
+      p0 += fabs(static_cast<double>(v) - static_cast<double>(x[r]));
+      if (is_dangling(dang, (int)r)) p1 += static_cast<double>(v);
+    }
+    // lanes of the same graph together, one atomic per graph present
+    const int key = live ? gid : -1;
+    unsigned rem = 0xffffffffu;
+    while (rem) {
+      const int lead = __ffs(rem) - 1;
+      const int k = __shfl_sync(0xffffffffu, key, lead);
+      const unsigned grp = __ballot_sync(0xffffffffu, key == k);
+      double s0 = key == k ? p0 : 0.0, s1 = key == k ? p1 : 0.0;
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      if (lane == lead && k >= 0 && (s0 != 0.0 || s1 != 0.0)) {
+        atomicAdd(acc + 2 * k, s0);
+        atomicAdd(acc + 2 * k + 1, s1);
+      }
+      rem &= ~grp;
+    }
+  }
+}
 
 // x = 1/n_g on graph g's rows; D_g = n_dangling_g / n_g; every graph active.
 template <typename T>
@@ -323,8 +362,6 @@ cudaError_t record_solve(merbit_batch_s* b, const T* vals, T* pi, double alpha, 
   bp.inv_n = b->inv_n;
   bp.D = b->D;
   bp.conv = b->conv;
-  bp.acc = b->acc;
-  bp.dang = p->dangling_bits;
   bp.alpha = alpha;
 
   // 1. initialisation, then the conditional node appended to the captured sequence
@@ -367,8 +404,15 @@ cudaError_t record_solve(merbit_batch_s* b, const T* vals, T* pi, double alpha, 
     EpiBatchPR<T> epi{};
     epi.p = bp;
     epi.out = half == 0 ? x1 : x0;
-    epi.xold = half == 0 ? x0 : x1;
-    e = launch_spmv<T, T, T>(p, vals, epi.xold, epi, cap);
+    const T* xin = half == 0 ? x0 : x1;
+    e = launch_spmv<T, T, T>(p, vals, xin, epi, cap);
+    if (e == cudaSuccess) {
+      const int64_t warps = (b->n + kRowsPerWarp - 1) / kRowsPerWarp;
+      const int rgrid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)sms * 8));
+      batch_reduce_kernel<T><<<rgrid, 256, 0, cap>>>(epi.out, xin, b->off, b->G, b->conv,
+                                                    p->dangling_bits, b->acc, p->red, b->n);
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
       batch_check_kernel<<<1, 1024, 0, cap>>>(b->G, tol, max_iter, b->acc, b->D, b->conv,
                                               b->last_r, b->bs, p->red, loop);

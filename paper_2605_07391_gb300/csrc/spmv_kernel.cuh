@@ -24,7 +24,6 @@
 #pragma once
 
 #include <algorithm>
-#include <type_traits>
 
 #include "merbit_internal.cuh"
 
@@ -133,12 +132,6 @@ __device__ __forceinline__ double read_reset(double* p) {
   return __longlong_as_double(
       static_cast<long long>(atomicExch(reinterpret_cast<unsigned long long*>(p), 0ull)));
 }
-
-// Epilogues with per-thread state (flush(p0, p1) at the end of each kernel) are detected here.
-template <typename E, typename = void>
-struct HasFlush : std::false_type {};
-template <typename E>
-struct HasFlush<E, std::void_t<decltype(&E::flush)>> : std::true_type {};
 
 // ---------------------------------------------------------------- epilogues
 // row(r, s)   : complete sum s of interior row r (accumulator type)
@@ -526,7 +519,6 @@ __global__ void __launch_bounds__(kThreads, 3)
       g.part[blockIdx.x] = make_double2(a, b);
     }
   }
-  if constexpr (HasFlush<Epi>::value) epi.flush(p0, p1);
 }
 
 // Grid-wide FP64 sums of (p0, p1) over a launch of blockDim.x <= 256 threads:
@@ -586,7 +578,6 @@ __global__ void __launch_bounds__(256) merbit_finalize_kernel(const Geometry g, 
     g.bnd_acc[k] = 0.0;
     epi.row64(r, tot, p0, p1);
   }
-  if constexpr (HasFlush<Epi>::value) epi.flush(p0, p1);
   if constexpr (Epi::kReduce) {
     for (int i = t0; i < nparts; i += stride) {
       const double2 q = g.part[i];
