@@ -326,6 +326,49 @@ def run_many_graphs(args, dev, stream) -> dict:
     return res
 
 
+def run_bicgstab(args, dev, stream) -> dict:
+    """BiCGSTAB (FP64) on A x = b, A the unit-valued adjacency of synthetic stand-ins for
+    the paper's graphs (a road network, a k-mer graph, a traffic trace with hubs),
+    b = A x_true with x_true ~ U[-1, 1], tol 1e-10, capped at --bicgstab-iters iterations.
+    Per iteration: two SpMVs (with fused dot products) and three vector passes; the
+    algorithmic bytes count each pass's reads and writes once."""
+    import torch
+
+    import inputs
+    import paper_2605_07391_gb300 as mb
+    hbm = peaks()[0]
+    cases = [("road_grid_2600x2600_k0.55", lambda: inputs.road_grid(2600, 2600, 0.55, 11)),
+             ("kmer_chains_10M", lambda: inputs.kmer_chains(10_000_000, 64, 0.02, 12)),
+             ("hub_rmat22_ef2", lambda: inputs.hub_graph(22, 2, 13))]
+    res = {"tol": 1e-10, "max_iter": args.bicgstab_iters}
+    for name, make in cases:
+        a = make()
+        n, nnz = a.n_rows, a.nnz
+        p = mb.plan(torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col).to(dev), n, n,
+                    stream=stream)
+        vals = torch.from_numpy(a.val).to(dev)
+        xt = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, n)).to(dev)
+        b = mb.spmv(p, vals, xt)
+        mb.bicgstab(p, vals, b, None, tol=1e-10, max_iter=3, stream=stream)        # warm
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        x, info = mb.bicgstab(p, vals, b, None, tol=1e-10, max_iter=args.bicgstab_iters, stream=stream)
+        torch.cuda.synchronize(dev)
+        ms = (time.perf_counter() - t0) * 1e3
+        inf = p.info()
+        spmv_bytes = 12 * nnz + 8 * n + 8 * n + 8 * n + 4 * inf.lane_num + 8 * (inf.tile_num + 1)
+        it_bytes = 2 * spmv_bytes + 8 * n * (4 + 3 + 7)
+        it = max(1, info["iters"])
+        res[name] = {"n": n, "nnz": nnz, "iters": info["iters"], "status": info["status"],
+                     "rel_resid": info["resid"], "ms": ms, "ms_per_iter": ms / it,
+                     "alg_bytes_per_iter": it_bytes, "alg_gbs": it_bytes * it / (ms * 1e-3) / 1e9,
+                     "roofline_frac": it_bytes * it / (ms * 1e-3) / 1e9 / hbm,
+                     "projected_s_for_20000_iters": ms / it * 20000 / 1e3}
+        del x, b, vals
+        p.destroy()
+    return res
+
+
 def run_autograd(args, dev, stream) -> dict:
     """dL/dvals for L = sum_i w_i pi_i (w ~ N(0, 1)) at the PageRank fixed point of the R-MAT
     scale 20 transition matrix, FP32: transpose + its plan (once per pattern), forward
@@ -401,6 +444,9 @@ def main():
     ap.add_argument("--no-many-graphs", action="store_true",
                     help="skip the many-graph run (256 R-MAT graphs, scales 10-20, one CUDA-graph launch)")
     ap.add_argument("--many-graphs", type=int, default=256, help="graphs in the many-graph run")
+    ap.add_argument("--no-bicgstab", action="store_true",
+                    help="skip the BiCGSTAB runs (road / k-mer / hub graph stand-ins)")
+    ap.add_argument("--bicgstab-iters", type=int, default=2000, help="iteration cap of the BiCGSTAB runs")
     ap.add_argument("--batched-k", type=int, nargs="+", default=[8, 32],
                     help="numbers of right-hand sides / seeds of the batched runs")
     ap.add_argument("--no-oracle-check", action="store_true")
@@ -582,6 +628,10 @@ def main():
         # ---- many graphs: PageRank of 256 uneven R-MAT graphs in one CUDA-graph launch
         if not args.no_many_graphs:
             out["many_graphs"] = run_many_graphs(args, dev, stream)
+
+        # ---- BiCGSTAB on undirected unit-valued graphs (the paper's second iterative workload)
+        if not args.no_bicgstab:
+            out["bicgstab"] = run_bicgstab(args, dev, stream)
 
         # ---- differentiation: PageRank value gradient by the implicit adjoint, R-MAT scale 20
         if not args.no_autograd:

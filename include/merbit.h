@@ -244,6 +244,23 @@ merbit_status merbit_autotune_sigma(const int32_t* row_ptr, const int32_t* col_i
                                     const int* candidates, int count, int reps, void* stream,
                                     int* best_sigma, float* ms_out);
 
+/*
+ * merbit_bicgstab — solves A x = b by unpreconditioned BiCGSTAB on the plan's SpMV (the
+ * paper's second iterative workload, Sec. 5.5), FP64: vals (16-byte aligned), b and x
+ * are device arrays of n; x holds the initial guess on entry and the last iterate on
+ * return.  Shadow residual r_hat = r_0; stops when ||b - A x||_2 <= tol ||b||_2 (the
+ * recurrence's residual), after max_iter iterations, or when a denominator of the
+ * recurrence is zero.  The whole solve is one CUDA-graph launch with a device-side loop
+ * (two SpMVs and three fused vector passes per iteration).  Outputs (may be NULL):
+ * iters_out, resid_out = ||r||_2 / ||b||_2 at the end, resid_hist (HOST, max_iter
+ * entries: the same after each iteration), status_out (1 converged, 2 max_iter,
+ * 3 breakdown).  Synchronous; allocates 6 n work vectors per call.  Errors: EINVAL,
+ * ENOTCONV (statuses 2 and 3; x holds the last iterate), EDEVICE, ENOMEM, ECUDA.
+ */
+merbit_status merbit_bicgstab(merbit_plan_t plan, const double* vals, const double* b, double* x,
+                              double tol, int max_iter, int* iters_out, double* resid_out,
+                              double* resid_hist, int* status_out, void* stream);
+
 /* ---------------------------------------------------------------- many graphs
  * PageRank of many independent graphs in one CUDA-graph launch (the batching extension;
  * no counterpart in the paper).  The graphs are the diagonal blocks of one block-diagonal

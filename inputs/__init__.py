@@ -175,6 +175,58 @@ def rmat_batch(num_graphs: int, seed: int, scales: tuple[int, int] = (10, 20),
     return csr, off
 
 
+# ---------------------------------------------------------------------------
+# Undirected graphs with unit values (the BiCGSTAB workload's matrices)
+# ---------------------------------------------------------------------------
+
+def undirected(n: int, u: np.ndarray, v: np.ndarray, name: str, meta: dict | None = None) -> CSR:
+    """Adjacency matrix (values 1) of the undirected graph with edges (u_i, v_i) on n
+    vertices; self loops and repeated edges dropped."""
+    bits = _bits(n)
+    u = np.asarray(u, np.uint64)
+    v = np.asarray(v, np.uint64)
+    b = np.uint64(bits)
+    keys = np.concatenate([(u << b) | v, (v << b) | u])
+    row_ptr, col = _from_keys(keys, n, n, bits, bits, True)
+    return CSR(n, n, row_ptr, col, np.ones(col.size), name, meta or {})
+
+
+def road_grid(nx: int, ny: int, keep: float = 0.6, seed: int = 11) -> CSR:
+    """Road-network stand-in: an nx x ny grid graph whose edges are kept independently
+    with probability `keep` (mean degree about 4 keep); vertex ids are row-major, so
+    neighbours are close in memory, as in geographically ordered road networks."""
+    rng = np.random.default_rng(seed)
+    idx = np.arange(nx * ny, dtype=np.int64).reshape(ny, nx)
+    u = np.concatenate([idx[:, :-1].ravel(), idx[:-1, :].ravel()])
+    v = np.concatenate([idx[:, 1:].ravel(), idx[1:, :].ravel()])
+    m = rng.random(u.size) < keep
+    return undirected(nx * ny, u[m], v[m], f"road{nx}x{ny}_k{keep}", {"seed": seed})
+
+
+def kmer_chains(n: int, mean_len: int = 64, extra: float = 0.02, seed: int = 12) -> CSR:
+    """k-mer-graph stand-in: the vertices in random order joined into paths of geometric
+    length (mean `mean_len`), plus extra*n random edges (mean degree about 2)."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(n).astype(np.int64)
+    keep = rng.random(n - 1) >= 1.0 / mean_len
+    u, v = perm[:-1][keep], perm[1:][keep]
+    k = int(extra * n)
+    eu, ev = rng.integers(0, n, k), rng.integers(0, n, k)
+    return undirected(n, np.concatenate([u, eu]), np.concatenate([v, ev]), f"kmer{n}", {"seed": seed})
+
+
+def hub_graph(scale: int, edge_factor: int = 2, seed: int = 13,
+              abc: tuple[float, float, float] = (0.7, 0.1, 0.1)) -> CSR:
+    """Traffic-trace stand-in: an undirected R-MAT graph with a strongly skewed degree
+    distribution (a few hubs adjacent to a large share of the vertices)."""
+    n = 1 << scale
+    keys = np.empty(edge_factor * n, np.uint64)
+    _lib().gen_rmat_keys(scale, keys.size, abc[0], abc[1], abc[2], seed, _p(keys))
+    sh = np.uint64(scale)
+    return undirected(n, keys >> sh, keys & np.uint64(n - 1), f"hub{scale}_ef{edge_factor}",
+                      {"seed": seed})
+
+
 def uniform_open0(n: int, seed: int, stream: int = 21) -> np.ndarray:
     """float64 values in (0, 1]."""
     out = np.empty(n, np.float64)

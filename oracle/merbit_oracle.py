@@ -12,7 +12,8 @@ path invariants, dense brute-force SpMV, closed-form PageRank vectors (n-cycle,
 bidirected star, in-star, 3-chain), closed-form personalised vectors (n-cycle,
 chain ending in a dangling vertex, bidirected star), dense linear solves of both
 fixed-point equations and of the adjoint equation, central finite differences of
-the PageRank loss and of g^T A x, and numpy's IEEE half conversion for the rounding helper.
+the PageRank loss and of g^T A x, and BiCGSTAB against a dense solve and scipy's
+implementation, and numpy's IEEE half conversion for the rounding helper.
 
 Readings of points the paper leaves open (each is also listed in the design
 notes):
@@ -28,6 +29,8 @@ notes):
     it stops when ||pi' - pi||_1 < tol (Sec. 5.5.1 leaves the rule open).
   * Personalised PageRank (the batching extension): one column per seed s, the
     teleport vector is e_s and the dangling mass also returns to s; pi_0 = e_s.
+  * BiCGSTAB: unpreconditioned, shadow residual r_hat = r_0, stop at
+    ||r||_2 <= tol ||b||_2 (Sec. 5.5 gives the tolerance but not the norm).
   * Differentiation (extension): every stored value of P^T is an independent
     parameter and the dangling set is fixed by the pattern; L = w^T pi gives
     dL/dA_ij = alpha lambda_i pi_j with (I - alpha M)^T lambda = w.
@@ -400,6 +403,53 @@ def pagerank_value_gradient(row_ptr, col, val, w, alpha: float = 0.85, tol: floa
     pi = pagerank(row_ptr, col, val, alpha, tol=tol, max_iter=100000)["pi"]
     lam = pagerank_adjoint(row_ptr, col, val, w, alpha, tol=tol)["lambda"]
     return {"grad": sddmm(row_ptr, col, lam, pi, alpha), "pi": pi, "lambda": lam}
+
+
+# ---------------------------------------------------------------------------
+# BiCGSTAB on the SpMV (Sec. 5.5: the second iterative workload)
+# ---------------------------------------------------------------------------
+
+def bicgstab(row_ptr, col, val, b, x0=None, tol: float = 1e-10, max_iter: int = 20000) -> dict:
+    """Unpreconditioned BiCGSTAB (van der Vorst) for A x = b in float64, shadow residual
+    r_hat = r_0, stopping when ||r||_2 <= tol ||b||_2 or after max_iter iterations.
+    Per iteration: rho = (r_hat, r); beta = (rho / rho_prev)(alpha / omega);
+    p = r + beta (p - omega v); v = A p; alpha = rho / (r_hat, v); s = r - alpha v;
+    t = A s; omega = (t, s) / (t, t); x += alpha p + omega s; r = s - omega t.
+    Returns x, the iterations, and ||r||_2 / ||b||_2 after each iteration."""
+    b = np.asarray(b, np.float64)
+    n = b.size
+    x = np.zeros(n) if x0 is None else np.asarray(x0, np.float64).copy()
+    r = b - spmv(row_ptr, col, val, x)[0]
+    r_hat = r.copy()
+    p = np.zeros(n)
+    v = np.zeros(n)
+    rho_prev = alpha = omega = 1.0
+    bnorm = float(np.linalg.norm(b))
+    hist = []
+    rho = float(r_hat @ r)
+    it = 0
+    if np.linalg.norm(r) <= tol * bnorm:
+        return {"x": x, "iters": 0, "resid": hist}
+    while it < max_iter:
+        beta = (rho / rho_prev) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = spmv(row_ptr, col, val, p)[0]
+        alpha = rho / float(r_hat @ v)
+        s = r - alpha * v
+        t = spmv(row_ptr, col, val, s)[0]
+        tt = float(t @ t)
+        omega = float(t @ s) / tt if tt > 0 else 0.0
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        it += 1
+        rel = float(np.linalg.norm(r)) / bnorm
+        hist.append(rel)
+        if rel <= tol or omega == 0.0:
+            break
+        rho_prev, rho = rho, float(r_hat @ r)
+        if rho == 0.0:
+            break
+    return {"x": x, "iters": it, "resid": hist}
 
 
 def relative_linf_error(pi, pi_star) -> float:

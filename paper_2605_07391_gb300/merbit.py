@@ -30,7 +30,8 @@ EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
            "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
            "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
-           "merbit_batch_get_plan", "merbit_batch_destroy", "merbit_autotune_sigma", "merbit_last_error",
+           "merbit_batch_get_plan", "merbit_batch_destroy", "merbit_autotune_sigma", "merbit_bicgstab",
+           "merbit_last_error",
            "merbit_version"]
 
 
@@ -96,6 +97,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_batch_pagerank": [vp, i32, vp, dbl, dbl, i32, vp, vp, vp, ctypes.POINTER(i32), vp],
             "merbit_autotune_sigma": [vp, vp, i64, i64, i64, i32, vp, vp, i32, i32, vp,
                                       ctypes.POINTER(i32), vp],
+            "merbit_bicgstab": [vp, vp, vp, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl),
+                                vp, ctypes.POINTER(i32), vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -337,6 +340,26 @@ def autotune_sigma(row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Ten
         cand.ctypes.data_as(ctypes.c_void_p), cand.size, reps, _stream(stream), ctypes.byref(best),
         ms.ctypes.data_as(ctypes.c_void_p)))
     return best.value, {int(c): float(t) for c, t in zip(cand, ms)}
+
+
+def bicgstab(p: "Plan", vals: torch.Tensor, b: torch.Tensor, x: torch.Tensor | None = None,
+             tol: float = 1e-10, max_iter: int = 20000, stream=None) -> tuple[torch.Tensor, dict]:
+    """merbit_bicgstab (FP64): x with ||b - A x||_2 <= tol ||b||_2.  x: initial guess
+    (zeros if None), overwritten.  Returns (x, {iters, resid, status, converged, hist})."""
+    _need_cuda(vals, b, x)
+    if vals.dtype != torch.float64 or b.dtype != torch.float64:
+        raise ValueError("bicgstab takes f64 vals and b")
+    if x is None:
+        x = torch.zeros_like(b)
+    iters, status = ctypes.c_int(0), ctypes.c_int(0)
+    resid = ctypes.c_double(0.0)
+    hist = np.zeros(max_iter, np.float64)
+    st = _check("merbit_bicgstab", load().merbit_bicgstab(
+        p.handle, _ptr(vals), _ptr(b), _ptr(x), tol, max_iter, ctypes.byref(iters),
+        ctypes.byref(resid), ctypes.c_void_p(hist.ctypes.data), ctypes.byref(status),
+        _stream(stream)), allow=(5,))
+    return x, {"iters": iters.value, "resid": resid.value, "status": status.value,
+               "converged": st == 0, "hist": hist[:iters.value].copy()}
 
 
 def transpose(row_ptr, col_idx, n_rows=None, n_cols=None, stream=None) -> Transpose:

@@ -1,3 +1,4 @@
+import pytest
 """Seeded input generators: determinism and the structure the configurations state."""
 import numpy as np
 
@@ -71,3 +72,18 @@ def test_block_diagonal_of_small_graphs():
     for r in range(7):
         dense[r, a.col[a.row_ptr[r]:a.row_ptr[r + 1]]] = a.val[a.row_ptr[r]:a.row_ptr[r + 1]]
     assert dense[1, 0] == 1.0 and dense[3, 4] == 1.0 and dense[6, 6] == 1.0
+
+
+@pytest.mark.parametrize("make", [lambda: inputs.road_grid(40, 30, 0.6, 1),
+                                  lambda: inputs.kmer_chains(5000, 32, 0.02, 2),
+                                  lambda: inputs.hub_graph(12, 2, 3)])
+def test_undirected_graphs_are_symmetric_unit(make):
+    a = make().check()
+    assert np.all(a.val == 1.0)
+    dense = np.zeros((a.n_rows, a.n_cols), bool)
+    rows = np.repeat(np.arange(a.n_rows), np.diff(a.row_ptr))
+    dense[rows, a.col] = True
+    assert np.array_equal(dense, dense.T) and not dense.diagonal().any()
+    for r in range(a.n_rows):
+        seg = a.col[a.row_ptr[r]:a.row_ptr[r + 1]]
+        assert np.all(np.diff(seg) > 0)

@@ -489,6 +489,58 @@ def test_pagerank_gradient_central_differences_rmat():
         assert abs(fd - grad[k]) <= 1e-4 * abs(grad[k]) + 1e-9, (k, fd, grad[k])
 
 
+# BiCGSTAB
+
+def _csr_of_dense(d):
+    return inputs.from_dense(np.asarray(d, np.float64))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bicgstab_matches_dense_solve(seed):
+    rng = np.random.default_rng(seed)
+    n = 40
+    d = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.2) + np.diag(rng.uniform(3, 5, n))
+    a = _csr_of_dense(d)
+    b = rng.standard_normal(n)
+    r = oracle.bicgstab(a.row_ptr, a.col, a.val, b, tol=1e-13, max_iter=500)
+    np.testing.assert_allclose(r["x"], np.linalg.solve(d, b), rtol=1e-10, atol=1e-11)
+    assert r["resid"][-1] <= 1e-13
+    assert abs(np.linalg.norm(b - d @ r["x"]) / np.linalg.norm(b) - r["resid"][-1]) < 1e-13
+
+
+def test_bicgstab_diagonal_converges_in_one_iteration():
+    d = np.diag(np.arange(1.0, 9.0))
+    a = _csr_of_dense(d)
+    b = np.ones(8)
+    r = oracle.bicgstab(a.row_ptr, a.col, a.val, b, tol=1e-12)
+    # the first step's minimal-residual correction solves a diagonal system of 8 distinct
+    # eigenvalues only approximately; it converges in at most 8 iterations and exactly
+    assert r["iters"] <= 8
+    np.testing.assert_allclose(r["x"], 1.0 / np.arange(1.0, 9.0), rtol=1e-10)
+    e = np.eye(8) * 2.5
+    r = oracle.bicgstab(*(lambda c: (c.row_ptr, c.col, c.val))(_csr_of_dense(e)), b, tol=1e-14)
+    assert r["iters"] == 1 and np.allclose(r["x"], 0.4)
+
+
+def test_bicgstab_matches_scipy():
+    """The same recurrence as scipy's bicgstab (shadow residual r_0): the same number of
+    iterations to the same relative tolerance, and close iterates."""
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    sp = pytest.importorskip("scipy.sparse")
+    a = inputs.road_grid(30, 20, 0.7, 3)
+    rng = np.random.default_rng(1)
+    xt = rng.uniform(-1, 1, a.n_rows)
+    b = oracle.spmv(a.row_ptr, a.col, a.val, xt)[0]
+    mine = oracle.bicgstab(a.row_ptr, a.col, a.val, b, tol=1e-8, max_iter=2000)
+    A = sp.csr_matrix((a.val, a.col, a.row_ptr), shape=(a.n_rows, a.n_cols))
+    count = [0]
+    x, info = spla.bicgstab(A, b, rtol=1e-8, atol=0.0, maxiter=2000,
+                            callback=lambda _x: count.__setitem__(0, count[0] + 1))
+    assert info == 0 and mine["resid"][-1] <= 1e-8
+    assert abs(mine["iters"] - count[0]) <= 1
+    assert np.linalg.norm(mine["x"] - x) <= 1e-6 * np.linalg.norm(x)
+
+
 def test_relative_linf_error():
     assert oracle.relative_linf_error([1.0, 2.2], [1.0, 2.0]) == pytest.approx(0.1)
 
