@@ -166,6 +166,18 @@ def oracle_sample_rate(a, budget_s: float, x64: np.ndarray, start_row: int = 0):
     return nnz_done, t_used
 
 
+def oracle_timed(fn, unit_count: float, unit: str, sample: str, budget_s: float = 3.0) -> dict:
+    """Run fn() (one bounded piece of oracle work worth unit_count units) until budget_s is
+    spent; the rate is units per second on one host core (numpy is single-threaded)."""
+    done, t_used = 0.0, 0.0
+    while t_used < budget_s:
+        t0 = time.perf_counter()
+        fn()
+        t_used += time.perf_counter() - t0
+        done += unit_count
+    return {"value": done / t_used, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the float64 CPU oracle on bounded samples of the same workload."""
     if rank != 0:
@@ -259,6 +271,15 @@ def run_batched(args, dev, stream) -> dict:
             Pi = r["pi"][:, [0, k - 1]].double().cpu().numpy()
             rr = oracle.ppr_residual(a.row_ptr, a.col, a.val, Pi, [int(seeds[0]), int(seeds[k - 1])], 0.85)
             rec["ppr_oracle_l1_residual_cols_0_last"] = [float(v) for v in rr]
+        if not args.no_oracle_check:
+            import oracle
+            r1 = a.n_rows // 256
+            lo, hi = 0, int(a.row_ptr[r1])
+            Xs = np.random.default_rng(3).random((a.n_cols, k))
+            rec["oracle"] = oracle_timed(
+                lambda: oracle.spmm(a.row_ptr[:r1 + 1].astype(np.int64), a.col[lo:hi], a.val[lo:hi], Xs),
+                (hi - lo) * k / 1e9, "Gnnz*vec/s",
+                f"float64 oracle SpMM, first 1/256 of the rows ({hi - lo} nnz) x {k} columns")
         res[f"k{k}"] = rec
         del r
     p.destroy()
@@ -290,6 +311,7 @@ def run_many_graphs(args, dev, stream) -> dict:
     b = mb.Batch(rp, col, off, sigma=best, stream=stream)
     torch.cuda.synchronize(dev)
     res["plan_ms"] = (time.perf_counter() - t0) * 1e3
+    b_plan_info = b.plan_info()
     pi = torch.empty(a.n_rows, dtype=torch.float64, device=dev)
     t0 = time.perf_counter()
     _, info = b.pagerank(vals, 0.85, tol=1e-8, max_iter=500, pi=pi, stream=stream)
@@ -307,7 +329,6 @@ def run_many_graphs(args, dev, stream) -> dict:
                 "updates_min_median_max": [int(info["iters"].min()), int(np.median(info["iters"])),
                                            int(info["iters"].max())],
                 "useful_gnnz_s": useful / (ms * 1e-3) / 1e9,
-                "executed_gnnz_s": info["rounds"] * a.nnz / (ms * 1e-3) / 1e9,
                 "max_resid": float(info["resid"].max())})
     if not args.no_oracle_check:
         import oracle
@@ -322,6 +343,26 @@ def run_many_graphs(args, dev, stream) -> dict:
                                          a.val[k0:k1], pin[lo:hi], 0.85)
             checks[f"graph{g}_n{hi - lo}"] = r
         res["oracle_l1_residual"] = checks
+        g0 = int(np.argsort(sizes)[len(sizes) // 2])
+        lo, hi = int(off[g0]), int(off[g0 + 1])
+        k0, k1 = int(a.row_ptr[lo]), int(a.row_ptr[hi])
+        sub = (a.row_ptr[lo:hi + 1] - a.row_ptr[lo], a.col[k0:k1] - lo, a.val[k0:k1])
+        upd = int(info["iters"][g0])
+        res["oracle"] = oracle_timed(lambda: oracle.pagerank(*sub, 0.85, tol=0.0, fixed_iters=upd),
+                                     upd * (k1 - k0) / 1e9, "Gnnz/s",
+                                     f"float64 oracle PageRank of graph {g0} ({hi - lo} vertices, "
+                                     f"{k1 - k0} nnz, {upd} updates)")
+    # algorithmic bytes of one update of graph g: FP64 values and int32 columns (12 B per
+    # nonzero), x gathered once, y written, and y and x read by the residual pass (32 B per
+    # vertex), plus its share of the plan's lane descriptors and tile coordinates
+    hbm = peaks()[0]
+    inf = b_plan_info
+    n_g = np.diff(off).astype(np.int64)
+    plan_b = (4 * inf.lane_num + 8 * (inf.tile_num + 1)) * (nnz_g + n_g) / (a.nnz + a.n_rows)
+    useful_bytes = float((info["iters"].astype(np.int64) * (12 * nnz_g + 32 * n_g) + info["iters"] * plan_b).sum())
+    res["useful_alg_bytes"] = useful_bytes
+    res["roofline"] = {"bound": "hbm", "achieved": useful_bytes / (ms * 1e-3) / 1e9, "peak": hbm,
+                       "unit": "GB/s", "frac": useful_bytes / (ms * 1e-3) / 1e9 / hbm}
     b.destroy()
     return res
 
@@ -366,6 +407,14 @@ def run_bicgstab(args, dev, stream) -> dict:
                      "projected_s_for_20000_iters": ms / it * 20000 / 1e3}
         del x, b, vals
         p.destroy()
+        if not args.no_oracle_check and name.startswith("road"):
+            import oracle
+            sm = inputs.road_grid(400, 400, 0.55, 11)
+            bs = oracle.spmv(sm.row_ptr, sm.col, sm.val, np.random.default_rng(1).uniform(-1, 1, sm.n_rows))[0]
+            res["oracle"] = oracle_timed(
+                lambda: oracle.bicgstab(sm.row_ptr, sm.col, sm.val, bs, tol=1e-30, max_iter=20),
+                20 * sm.n_rows / 1e6, "Mrow-iterations/s",
+                f"float64 oracle BiCGSTAB, 20 iterations on a 400x400 road grid ({sm.nnz} nnz)")
     return res
 
 
@@ -424,6 +473,14 @@ def run_autograd(args, dev, stream) -> dict:
                      "autograd_forward_backward_ms": e2e}
     res["f32_vs_f64_grad_rel_l1"] = float((grads["f32"] - grads["f64"]).abs().sum() / grads["f64"].abs().sum())
     A.plan.destroy()
+    if not args.no_oracle_check:
+        import oracle
+        s14 = inputs.rmat_transition(14, 16, 3)
+        w14 = np.random.default_rng(20).standard_normal(s14.n_rows)
+        res["oracle"] = oracle_timed(
+            lambda: oracle.pagerank_value_gradient(s14.row_ptr, s14.col, s14.val, w14, 0.85, tol=1e-12),
+            1.0, "gradients/s", f"float64 oracle value gradient (forward + adjoint to 1e-12) of the "
+            f"R-MAT scale 14 transition matrix ({s14.nnz} nnz)", budget_s=2.0)
     return res
 
 

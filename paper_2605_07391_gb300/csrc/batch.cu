@@ -64,6 +64,8 @@ struct EpiBatchPR {
   static constexpr bool kReduce = false;
   BatchParams p;
   T* out;
+  const int32_t* block_list;   // blocks touching a graph that has not converged
+  const int* block_count;
   mutable int lo, hi;
   mutable bool frozen;
   mutable T a, tele;
@@ -94,6 +96,80 @@ struct EpiBatchPR {
   }
   __device__ __forceinline__ void finish(double, double, RedState*) const {}
 };
+
+// The blocks of the plan whose rows touch a graph that has not converged, in increasing
+// order (so the CTAs still sweep the matrix front to back and share x in L2).  A block is
+// skipped only when every graph among its rows [y_bs, y_be] has converged, so a row it
+// shares with a neighbouring block belongs to a converged graph that no kernel writes any
+// more.  Two passes: per chunk of kCompactChunk blocks the flags and their count, then
+// every chunk writes its active blocks at the offset the counts before it give.
+constexpr int kCompactChunk = 2048;
+
+__device__ __forceinline__ bool block_active(const uint32_t* tile_y, int tile_num, int64_t n,
+                                             const int32_t* off, int G, const int* conv, int v) {
+  const int bs = v * kTilesPerBlock;
+  const int be = min(bs + kTilesPerBlock, tile_num);
+  const int64_t y0 = tile_y[bs] & ~kMsb;
+  int64_t y1 = tile_y[be] & ~kMsb;
+  if (y1 >= n) y1 = n - 1;
+  const int g0 = y0 < n ? graph_of(off, G, (int)y0) : G - 1;
+  const int g1 = graph_of(off, G, (int)y1);
+  for (int g = g0; g <= g1; ++g)
+    if (conv[g] < 0) return true;
+  return false;
+}
+
+__global__ void __launch_bounds__(256)
+    batch_flags_kernel(const uint32_t* tile_y, int tile_num, int nb, int64_t n, const int32_t* off,
+                       int G, const int* conv, uint8_t* flags, int* chunk_count) {
+  int mine = 0;
+  const int c0 = blockIdx.x * kCompactChunk;
+  for (int i = threadIdx.x; i < kCompactChunk; i += blockDim.x) {
+    const int v = c0 + i;
+    if (v >= nb) break;
+    const bool a = block_active(tile_y, tile_num, n, off, G, conv, v);
+    flags[v] = a ? 1 : 0;
+    mine += a;
+  }
+  __shared__ int sum;
+  if (threadIdx.x == 0) sum = 0;
+  __syncthreads();
+  atomicAdd(&sum, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) chunk_count[blockIdx.x] = sum;
+}
+
+__global__ void __launch_bounds__(256)
+    batch_list_kernel(const uint8_t* flags, const int* chunk_count, int nb, int32_t* list,
+                      int* count) {
+  __shared__ int base;
+  __shared__ int warp_tot[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int c = 0; c < (int)blockIdx.x; ++c) s += chunk_count[c];
+    base = s;
+    if (blockIdx.x == gridDim.x - 1) *count = s + chunk_count[blockIdx.x];
+  }
+  __syncthreads();
+  const int c0 = blockIdx.x * kCompactChunk;
+  for (int r0 = 0; r0 < kCompactChunk; r0 += blockDim.x) {
+    const int v = c0 + r0 + (int)threadIdx.x;
+    const bool a = v < nb && flags[v];
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < warp) before += warp_tot[w];
+      all += warp_tot[w];
+    }
+    if (a) list[base + before + __popc(m & ((1u << lane) - 1u))] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) base += all;
+    __syncthreads();
+  }
+}
 
 constexpr int kRowsPerWarp = 2048;
 
@@ -312,6 +388,10 @@ struct merbit_batch_s {
   double* acc = nullptr;
   double* last_r = nullptr;
   BatchState* bs = nullptr;
+  int32_t* blist = nullptr;      // active blocks of the current round, in order
+  int* bcount = nullptr;
+  uint8_t* bflags = nullptr;     // per block: touches an active graph
+  int* ccount = nullptr;         // active blocks per chunk of kCompactChunk
   void* x1 = nullptr;
   size_t x1_bytes = 0;
   // the instantiated solve and what it was built for
@@ -339,6 +419,10 @@ void free_batch(merbit_batch_s* b) {
   cudaFree(b->acc);
   cudaFree(b->last_r);
   cudaFree(b->bs);
+  cudaFree(b->blist);
+  cudaFree(b->bcount);
+  cudaFree(b->bflags);
+  cudaFree(b->ccount);
   cudaFree(b->x1);
   delete b;
 }
@@ -404,6 +488,17 @@ cudaError_t record_solve(merbit_batch_s* b, const T* vals, T* pi, double alpha, 
     EpiBatchPR<T> epi{};
     epi.p = bp;
     epi.out = half == 0 ? x1 : x0;
+    epi.block_list = b->blist;
+    epi.block_count = b->bcount;
+    if (p->nb > 0) {
+      const int chunks = (int)((p->nb + kCompactChunk - 1) / kCompactChunk);
+      batch_flags_kernel<<<chunks, 256, 0, cap>>>(p->tile_y, (int)p->tile_num, (int)p->nb, b->n,
+                                                   b->off, b->G, b->conv, b->bflags, b->ccount);
+      batch_list_kernel<<<chunks, 256, 0, cap>>>(b->bflags, b->ccount, (int)p->nb, b->blist,
+                                                  b->bcount);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) break;
+    }
     const T* xin = half == 0 ? x0 : x1;
     e = launch_spmv<T, T, T>(p, vals, xin, epi, cap);
     if (e == cudaSuccess) {
@@ -466,6 +561,10 @@ merbit_status merbit_batch_plan(const int32_t* row_ptr, const int32_t* col_idx, 
   A((void**)&b->acc, sizeof(double) * 2 * G);
   A((void**)&b->last_r, sizeof(double) * G);
   A((void**)&b->bs, sizeof(BatchState));
+  A((void**)&b->blist, sizeof(int32_t) * (size_t)std::max<int64_t>(p->nb, 1));
+  A((void**)&b->bcount, sizeof(int));
+  A((void**)&b->bflags, (size_t)std::max<int64_t>(p->nb, 1));
+  A((void**)&b->ccount, sizeof(int) * (size_t)std::max<int64_t>((p->nb + kCompactChunk - 1) / kCompactChunk, 1));
   unsigned long long* cnt = nullptr;
   int* err = nullptr;
   A((void**)&cnt, sizeof(unsigned long long) * G);

@@ -24,6 +24,8 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
+#include <utility>
 
 #include "merbit_internal.cuh"
 
@@ -132,6 +134,14 @@ __device__ __forceinline__ double read_reset(double* p) {
   return __longlong_as_double(
       static_cast<long long>(atomicExch(reinterpret_cast<unsigned long long*>(p), 0ull)));
 }
+
+// An epilogue with members block_list / block_count makes the kernel process only the
+// listed blocks (*block_count of them, read at kernel start): iterative drivers use it to
+// skip blocks whose rows no longer change.
+template <typename E, typename = void>
+struct HasBlockList : std::false_type {};
+template <typename E>
+struct HasBlockList<E, std::void_t<decltype(std::declval<E&>().block_list)>> : std::true_type {};
 
 // ---------------------------------------------------------------- epilogues
 // row(r, s)   : complete sum s of interior row r (accumulator type)
@@ -348,6 +358,14 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (bc) bulk_g2s(sc(s), g.col + in.a0c, bc, &mbar[s], pol_stream);
   };
 
+  // the k-th block to process: all blocks in order, or the epilogue's list
+  int nbl = g.nb;
+  if constexpr (HasBlockList<Epi>::value) nbl = *reinterpret_cast<const volatile int*>(epi.block_count);
+  auto blk = [&](int k) -> int {
+    if constexpr (HasBlockList<Epi>::value) return __ldg(epi.block_list + k);
+    else return k;
+  };
+
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
@@ -356,13 +374,14 @@ __global__ void __launch_bounds__(kThreads, 3)
   __syncthreads();
   if (tid == 0) {
     int xb, xe; uint32_t yb, ye;
-    if (blockIdx.x < g.nb) { geom_of(blockIdx.x, xb, xe, yb, ye); issue(0, xb, xe, yb, ye); }
-    if (blockIdx.x + G < g.nb) { geom_of(blockIdx.x + G, xb, xe, yb, ye); issue(1, xb, xe, yb, ye); }
+    if (blockIdx.x < nbl) { geom_of(blk(blockIdx.x), xb, xe, yb, ye); issue(0, xb, xe, yb, ye); }
+    if (blockIdx.x + G < nbl) { geom_of(blk(blockIdx.x + G), xb, xe, yb, ye); issue(1, xb, xe, yb, ye); }
   }
 
   double p0 = 0.0, p1 = 0.0;
   int it = 0;
-  for (int v = blockIdx.x; v < g.nb; v += G, ++it) {
+  for (int kb = blockIdx.x; kb < nbl; kb += G, ++it) {
+    const int v = blk(kb);
     const int s = it & 1;
     const uint32_t par = (it >> 1) & 1;
 
@@ -379,15 +398,15 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
     // geometry for the copy issued at the end of this iteration
     int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
-    const bool refill = (tid == 0) && (v + 2 * G < g.nb);
-    if (refill) geom_of(v + 2 * G, nxb, nxe, nyb, nye);
+    const bool refill = (tid == 0) && (kb + 2 * G < nbl);
+    if (refill) geom_of(blk(kb + 2 * G), nxb, nxe, nyb, nye);
 
     const bool ok = mbar_wait_bounded(&mbar[s], par);
     if (__syncthreads_or(!ok)) {
       // expired wait: record it, let this CTA's copies land (bounded), leave
       if (tid == 0) atomicOr(&g.red->err, 1);
       mbar_wait_bounded(&mbar[s], par);
-      if (v + G < g.nb) mbar_wait_bounded(&mbar[s ^ 1], ((it + 1) >> 1) & 1);
+      if (kb + G < nbl) mbar_wait_bounded(&mbar[s ^ 1], ((it + 1) >> 1) & 1);
       return;
     }
     const StageInfo in = info[s];

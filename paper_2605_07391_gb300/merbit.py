@@ -297,6 +297,13 @@ class Batch:
             raise MerbitError("batch", 1, "batch was destroyed")
         return self._handle
 
+    def plan_info(self) -> PlanInfo:
+        """merbit_plan_get_info of the batch's plan (owned by the batch)."""
+        inf = PlanInfo()
+        h = ctypes.c_void_p(load().merbit_batch_get_plan(self.handle))
+        _check("merbit_plan_get_info", load().merbit_plan_get_info(h, ctypes.byref(inf)))
+        return inf
+
     def pagerank(self, vals: torch.Tensor, alpha: float = 0.85, tol: float = 1e-8,
                  max_iter: int = 1000, pi: torch.Tensor | None = None, stream=None):
         """merbit_batch_pagerank.  Returns (pi, info) with per-graph iters and resid."""
