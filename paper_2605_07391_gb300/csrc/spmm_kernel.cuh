@@ -108,15 +108,18 @@ struct SpmmGeometry {
   int kc;           // columns in this chunk (a multiple of VW)
 };
 
+// Two CTAs per SM: the register room (up to 128 per thread) keeps a whole batch of gathers
+// in flight; capping registers for three CTAs per SM serialised them (k = 8: 1.04 ms vs
+// 0.67 ms on R-MAT scale 22).
 template <int KC, int VW, typename Epi>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 2)
     merbit_spmm_kernel(const Geometry g, const SpmmGeometry sg, const float* __restrict__ vals,
                        const float* __restrict__ X, int ldx, Epi epi) {
   using V = SpmmVec<VW>;
   using VT = typename V::T;
   constexpr int T = KC / VW;                   // threads per chunk row
   constexpr int GRP = 32 / T;                  // groups per warp
-  constexpr int U = VW == 4 ? 8 : 16;          // row slices gathered per batch
+  constexpr int U = VW == 4 ? (KC == 32 ? 12 : 8) : 16;   // row slices gathered per batch
   constexpr int VE = 4;
   constexpr int kEnds = kOmega * kSigmaMax;    // most row ends in one tile
   __shared__ __align__(8) uint64_t mbar[2];
