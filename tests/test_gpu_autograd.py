@@ -165,3 +165,18 @@ def test_pagerank_gradient_rmat20(cuda_device):
         fd = (lp - lm) / (2 * h)
         assert abs(fd - ref[k]) <= 2e-3 * abs(ref[k]) + 1e-10, (k, fd, ref[k])
         assert abs(g32[k] - ref[k]) <= 1e-2 * abs(ref[k]) + 1e-10, (k, g32[k], ref[k])
+
+
+def test_gradcheck_spmv_and_pagerank(cuda_device):
+    """torch.autograd.gradcheck of both wrappers in FP64 on small graphs: the analytic
+    backward (transpose SpMV, per-nonzero products, adjoint solve) against torch's own
+    central differences of the forward."""
+    a = inputs.random_graph_transition(24, 0.15, 8)
+    A = ag.Matrix(*_dev(a), a.n_rows, a.n_cols)
+    rng = np.random.default_rng(8)
+    vals = torch.from_numpy(a.val).cuda().requires_grad_()
+    x = torch.from_numpy(rng.random(a.n_cols)).cuda().requires_grad_()
+    assert torch.autograd.gradcheck(lambda v, xx: ag.spmv(A, v, xx), (vals, x), eps=1e-6, atol=1e-8)
+    w = torch.from_numpy(rng.standard_normal(a.n_rows)).cuda()
+    assert torch.autograd.gradcheck(lambda v: (ag.pagerank(A, v, 0.85, tol=1e-14) * w).sum(), (vals,),
+                                    eps=1e-6, atol=1e-8)

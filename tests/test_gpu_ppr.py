@@ -141,3 +141,15 @@ def test_ppr_full_rmat22(cuda_device, k):
     res = oracle.ppr_residual(a.row_ptr, a.col, a.val, Pi[:, cols], [int(seeds[c]) for c in cols],
                               ALPHA)
     assert res.max() < 5e-6, res
+
+
+@pytest.mark.parametrize("k", [300, 516])
+def test_ppr_many_seeds(cuda_device, k):
+    """Wide batches: k = 300 takes the scalar path with one row of 300 threads per block of
+    the streaming pass, k = 516 the 16-byte path with 129 column vectors per row."""
+    a = inputs.rmat_transition(10, 16, 4)
+    seeds = inputs.ppr_seeds(a, k, 9)
+    Pi, r = _ppr(a, seeds, tol=0.0, max_iter=12)
+    ref = oracle.personalized_pagerank(a.row_ptr, a.col, a.val, seeds, ALPHA, fixed_iters=12)
+    assert np.abs(Pi - ref["pi"]).sum(axis=0).max() < 2e-5
+    np.testing.assert_allclose(r["resid"], ref["last"], rtol=1e-3, atol=1e-6)

@@ -83,3 +83,8 @@ def test_spmm_full_rmat22(cuda_device, k):
     colsum = np.bincount(a.col, weights=vh, minlength=a.n_cols)
     tot = colsum @ Xh
     assert np.allclose(Yh.sum(axis=0), tot, rtol=1e-5)
+
+
+def test_spmm_wide(cuda_device):
+    """k = 300: nine 32-column chunks and a 12-column remainder in a 16-column chunk."""
+    _run(inputs.rmat_transition(11, 16, 5), 300)
