@@ -507,7 +507,8 @@ def main():
     ap.add_argument("--batched-k", type=int, nargs="+", default=[8, 32],
                     help="numbers of right-hand sides / seeds of the batched runs")
     ap.add_argument("--no-oracle-check", action="store_true")
-    ap.add_argument("--inner-sweeps", type=int, default=32, help="max inner sweeps per refinement step")
+    ap.add_argument("--inner-sweeps", type=int, default=0,
+                    help="max inner sweeps per refinement step (0: the tuned setting of each mode)")
     ap.add_argument("--sigma", type=int, default=14, help="steps per lane of the plan")
     args = ap.parse_args()
     rank, world, local = dist_setup()
@@ -649,11 +650,17 @@ def main():
             pr = {}
             runs = [("ir_bf16", torch.float64), ("ir_f16", torch.float64), ("ir_f32", torch.float64),
                     ("plain_f64", torch.float64), ("plain_f32", torch.float32)]
+            # refinement settings (inner stop eta, sweep cap) tuned per mode on this workload:
+            # a sweep of the eta x cap grid, both the reduced-precision and the FP32 modes
+            tuned = {"ir_bf16": (2.0 ** -4, 12), "ir_f16": (2.0 ** -11, 6), "ir_f32": (2.0 ** -10, 6)}
             for name, dt in runs:
                 mode = "plain" if name.startswith("plain") else name
                 vals = v64 if dt == torch.float64 else v32
+                eta, cap = tuned.get(mode, (0.0, 32))
+                if args.inner_sweeps:
+                    eta, cap = 0.0, args.inner_sweeps
                 kw = dict(tol=1e-10, max_iter=400 if mode == "plain" else 60, mode=mode,
-                          inner_sweeps=args.inner_sweeps, stream=stream)
+                          inner_sweeps=cap, inner_tol=eta, stream=stream)
                 mb.pagerank(p, vals, 0.85, **dict(kw, max_iter=2, tol=0.0))   # warm
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
@@ -664,7 +671,8 @@ def main():
                        "converged": info["converged"], "end_to_end_ms": ms + plan_ms,
                        "spmv_launches": info["spmv_launches"]}
                 if mode != "plain":
-                    rec["inner_sweeps"] = args.inner_sweeps
+                    rec["inner_sweeps_cap"] = cap
+                    rec["inner_eta"] = eta
                 if not args.no_oracle_check:
                     pin = pi.double().cpu().numpy()
                     r = oracle.pagerank_residual(a.row_ptr, a.col, a.val, pin, 0.85)
