@@ -312,6 +312,19 @@ merbit_status merbit_spmv_host(merbit_plan_t plan, merbit_dtype dtype, const voi
                                const void* x_host, void* y_host, void* stream);
 
 /*
+ * merbit_spmv_host_async — as merbit_spmv_host (F32 or F64, x and y in HOST memory,
+ * vals on the device) but without waiting: the call uploads x into one of two plan-owned
+ * staging slots and runs the product on `stream`, and an internal copy stream downloads
+ * y once the product is done, so consecutive calls overlap one call's download with the
+ * next call's upload and product.  With pageable host memory the copies serialise.
+ * x_host must stay unchanged and y_host unread until merbit_plan_sync returns (it waits
+ * for every pending download of the plan).  Errors: EINVAL, ENOMEM, ECUDA, and those of
+ * merbit_spmv_ex.
+ */
+merbit_status merbit_spmv_host_async(merbit_plan_t plan, merbit_dtype dtype, const void* vals,
+                                     const void* x_host, void* y_host, void* stream);
+
+/*
  * merbit_vals_convert — round nnz values (src_dtype F64 or F32) to dst_dtype
  * (BF16, F16 or F32), round-to-nearest-even.  With auto_scale != 0 and dst F16
  * the values are first multiplied by 2^k, k the largest power keeping

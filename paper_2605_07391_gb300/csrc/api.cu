@@ -10,6 +10,8 @@
 #include "extensions.cuh"
 
 namespace merbit {
+cudaError_t host_async_wait(const merbit_plan_s* p);
+void host_async_release(const merbit_plan_s* p);
 cudaError_t build_tiles(const merbit_plan_s* p, const int32_t* row_ptr, cudaStream_t st);
 cudaError_t build_dangling(merbit_plan_s* p, cudaStream_t st, unsigned long long* host_count);
 }  // namespace merbit
@@ -55,6 +57,7 @@ size_t dtype_size(merbit_dtype d) {
 
 void free_plan(merbit_plan_s* p) {
   if (!p) return;
+  host_async_release(p);
   cudaFree(p->tile_x);
   cudaFree(p->tile_y);
   cudaFree(p->lane_desc);
@@ -413,6 +416,7 @@ merbit_status merbit_plan_export(merbit_plan_t p, uint32_t* tile_x, uint32_t* ti
 merbit_status merbit_plan_sync(merbit_plan_t p, void* stream) {
   if (merbit_status s = check_plan(p)) return s;
   cudaStream_t st = as_stream(stream);
+  MB_TRY(host_async_wait(p));
   StateWord w{};
   MB_TRY(read_state(p, st, &w));
   if (w.err) {

@@ -26,7 +26,7 @@ _TORCH_DT = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch
 
 EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_get_info",
            "merbit_plan_sync", "merbit_plan_export", "merbit_spmv", "merbit_spmv_ex", "merbit_spmm",
-           "merbit_ppr", "merbit_spmv_host",
+           "merbit_ppr", "merbit_spmv_host", "merbit_spmv_host_async",
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
            "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
            "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
@@ -79,6 +79,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_spmv": [vp, i32, vp, vp, vp],
             "merbit_spmv_ex": [vp, i32, i32, vp, vp, vp, i32, vp],
             "merbit_spmv_host": [vp, i32, vp, vp, vp, vp],
+            "merbit_spmv_host_async": [vp, i32, vp, vp, vp, vp],
             "merbit_spmm": [vp, vp, vp, vp, i64, i64, i64, vp],
             "merbit_ppr": [vp, vp, vp, i64, dbl, dbl, i32, vp, ctypes.POINTER(i32),
                            ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp],
@@ -478,15 +479,18 @@ def ppr(p: Plan, vals: torch.Tensor, seeds, alpha: float = 0.85, tol: float = 1e
 
 
 def spmv_host(p: Plan, vals: torch.Tensor, x_host: torch.Tensor, y_host: torch.Tensor | None = None,
-              stream=None) -> torch.Tensor:
-    """merbit_spmv_host: x and y in host memory (pinned recommended); synchronous."""
+              stream=None, wait: bool = True) -> torch.Tensor:
+    """merbit_spmv_host: x and y in host memory (pinned recommended); synchronous.  With
+    wait=False, merbit_spmv_host_async: returns at once and consecutive calls overlap;
+    call p.sync() before reading y_host or changing x_host."""
     _need_cuda(vals)
     if x_host.is_cuda:
         raise ValueError("x_host must be a CPU tensor")
     if y_host is None:
         y_host = torch.empty(p.n_rows, dtype=x_host.dtype, pin_memory=True)
-    _check("merbit_spmv_host", load().merbit_spmv_host(p.handle, _dt(vals), _ptr(vals),
-                                                      _ptr(x_host), _ptr(y_host), _stream(stream)))
+    name = "merbit_spmv_host" if wait else "merbit_spmv_host_async"
+    _check(name, getattr(load(), name)(p.handle, _dt(vals), _ptr(vals), _ptr(x_host), _ptr(y_host),
+                                      _stream(stream)))
     return y_host
 
 

@@ -155,6 +155,30 @@ def test_spmv_host_buffers(cuda_device, dtype):
     check_rel(y.double().numpy(), y_ref, d, TOL[dtype], "host")
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_spmv_host_async_overlapping_calls(cuda_device, dtype):
+    """merbit_spmv_host_async: six calls in flight with different host x and y buffers (the
+    two staging slots are reused three times each), then one sync; also a pageable pair."""
+    a = inputs.rmat_transition(14, 16, 2)
+    p, _ = make_plan(a)
+    vals = torch.from_numpy(a.val).to("cuda", dtype)
+    xs = [torch.from_numpy(inputs.uniform_vector(a.n_cols, 10 + i)).to(dtype).pin_memory() for i in range(6)]
+    ys = [torch.full((a.n_rows,), float("nan"), dtype=dtype).pin_memory() for _ in range(6)]
+    for x, y in zip(xs, ys):
+        mb.spmv_host(p, vals, x, y, wait=False)
+    p.sync()
+    for x, y in zip(xs, ys):
+        y_ref, d = oracle.spmv(a.row_ptr, a.col, as_f64(vals), x.double().numpy())
+        check_rel(y.double().numpy(), y_ref, d, TOL[dtype], "host async")
+    xp = torch.from_numpy(inputs.uniform_vector(a.n_cols, 30)).to(dtype)
+    yp = torch.empty(a.n_rows, dtype=dtype)
+    mb.spmv_host(p, vals, xp, yp, wait=False)
+    p.sync()
+    y_ref, d = oracle.spmv(a.row_ptr, a.col, as_f64(vals), xp.double().numpy())
+    check_rel(yp.double().numpy(), y_ref, d, TOL[dtype], "host async pageable")
+    p.destroy()
+
+
 def test_spmv_argument_errors(cuda_device):
     a = inputs.rmat_transition(10, 8, 1)
     p, _ = make_plan(a)
