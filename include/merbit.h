@@ -248,7 +248,8 @@ merbit_status merbit_autotune_sigma(const int32_t* row_ptr, const int32_t* col_i
  * merbit_bicgstab — solves A x = b by unpreconditioned BiCGSTAB on the plan's SpMV (the
  * paper's second iterative workload, Sec. 5.5), FP64: vals (16-byte aligned), b and x
  * are device arrays of n; x holds the initial guess on entry and the last iterate on
- * return.  Shadow residual r_hat = r_0; stops when ||b - A x||_2 <= tol ||b||_2 (the
+ * return.  vals NULL means every value is 1 (an adjacency pattern): the products then
+ * read no value stream.  Shadow residual r_hat = r_0; stops when ||b - A x||_2 <= tol ||b||_2 (the
  * recurrence's residual), after max_iter iterations, or when a denominator of the
  * recurrence is zero.  The whole solve is one CUDA-graph launch with a device-side loop
  * (two SpMVs and three fused vector passes per iteration).  Outputs (may be NULL):

@@ -10,6 +10,7 @@
 // FP64 reduction, so no step waits for the host.  The whole solve is one CUDA-graph
 // launch: r_0 = b - A x_0, then a conditional while node whose body is one iteration;
 // the stop test (||r||_2 <= tol ||b||_2, max_iter, or a zero denominator) ends the loop.
+// Without values (an adjacency pattern, all values 1) the SpMVs read no value stream.
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -181,6 +182,14 @@ __global__ void bicg_guard_kernel(BicgVecs w, RedState* red) {
   if (++w.st->body >= w.st->max_iter) stop(w, red, 2);
 }
 
+// the product of the plan's matrix, with values or (vals == NULL) all values 1
+template <typename Epi>
+cudaError_t spmv64(const merbit_plan_s* p, const double* vals, const double* x, const Epi& epi,
+                   cudaStream_t st) {
+  if (vals) return launch_spmv<double, double, double>(p, vals, x, epi, st);
+  return launch_spmv<UnitVal<double>, double, double>(p, nullptr, x, epi, st);
+}
+
 merbit_status bfail2(merbit_status s, const char* msg) {
   set_last_error(msg);
   return s;
@@ -205,8 +214,8 @@ merbit_status merbit_bicgstab(merbit_plan_t p, const double* vals, const double*
     if (status_out) *status_out = 1;
     return MERBIT_OK;
   }
-  if (!b || !x || (p->nnz > 0 && !vals)) return bfail2(MERBIT_EINVAL, "vals, b or x is NULL");
-  if (p->nnz > 0 && (reinterpret_cast<uintptr_t>(vals) & 15))
+  if (!b || !x) return bfail2(MERBIT_EINVAL, "b or x is NULL");
+  if (vals && (reinterpret_cast<uintptr_t>(vals) & 15))
     return bfail2(MERBIT_EINVAL, "vals must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t vb = (sizeof(double) * (size_t)n + 255) & ~size_t(255);
@@ -243,7 +252,7 @@ merbit_status merbit_bicgstab(merbit_plan_t p, const double* vals, const double*
     EpiBicgInit ei{};
     ei.w = w;
     ei.tol = tol;
-    if (e == cudaSuccess) e = launch_spmv<double, double, double>(p, vals, x, ei, cap);
+    if (e == cudaSuccess) e = spmv64(p, vals, x, ei, cap);
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
     cudaStreamCaptureStatus cs;
@@ -266,12 +275,12 @@ merbit_status merbit_bicgstab(merbit_plan_t p, const double* vals, const double*
     bicg_p_kernel<<<vgrid, 256, 0, cap>>>(w, n, p->red);
     EpiBicgV ev{};
     ev.w = w;
-    e = launch_spmv<double, double, double>(p, vals, w.p, ev, cap);
+    e = spmv64(p, vals, w.p, ev, cap);
     if (e == cudaSuccess) {
       bicg_s_kernel<<<vgrid, 256, 0, cap>>>(w, n, p->red);
       EpiBicgT et{};
       et.w = w;
-      e = launch_spmv<double, double, double>(p, vals, w.s, et, cap);
+      e = spmv64(p, vals, w.s, et, cap);
     }
     if (e == cudaSuccess) {
       bicg_xr_kernel<<<vgrid, 256, 0, cap>>>(w, n, p->red);

@@ -300,6 +300,18 @@ __host__ __device__ inline size_t stage_bytes(int sigma) {
   return stage_vals_bytes<VT>(sigma) + stage_col_bytes<VT>(sigma);
 }
 
+// A matrix whose stored values are all 1 (an adjacency pattern): no value stream is read
+// and a nonzero's product is x[col].  The type has the accumulator's width, so the
+// products take the place the values would have had in the stage.
+template <typename AT>
+struct UnitVal {
+  AT pad;
+};
+template <typename T>
+struct IsUnit : std::false_type {};
+template <typename AT>
+struct IsUnit<UnitVal<AT>> : std::true_type {};
+
 // Products go where an input of the same width was staged.
 template <typename VT, typename AT>
 struct ProdInVals {
@@ -351,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     in.a0c = xb & ~3;
     in.endc = max(in.a0c, min((xe + 3) & ~3, nnz_c));
     info[s] = in;
-    const uint32_t bv = (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT);
+    const uint32_t bv = IsUnit<VT>::value ? 0u : (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT);
     const uint32_t bc = (uint32_t)(in.endc - in.a0c) * 4u;
     mbar_arrive_expect_tx(&mbar[s], bv + bc);
     if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, &mbar[s], pol_stream);
@@ -439,8 +451,12 @@ __global__ void __launch_bounds__(kThreads, 3)
         const int e = tid + u * kThreads;
         if (e < cnt) {
           const int k = in.x_bs + e;
-          const AT v = static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
-          prod[k - pb] = v * xv[u];
+          if constexpr (IsUnit<VT>::value) {
+            prod[k - pb] = xv[u];
+          } else {
+            const AT v = static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
+            prod[k - pb] = v * xv[u];
+          }
         }
       }
     }

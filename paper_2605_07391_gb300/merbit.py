@@ -350,12 +350,13 @@ def autotune_sigma(row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Ten
     return best.value, {int(c): float(t) for c, t in zip(cand, ms)}
 
 
-def bicgstab(p: "Plan", vals: torch.Tensor, b: torch.Tensor, x: torch.Tensor | None = None,
+def bicgstab(p: "Plan", vals: torch.Tensor | None, b: torch.Tensor, x: torch.Tensor | None = None,
              tol: float = 1e-10, max_iter: int = 20000, stream=None) -> tuple[torch.Tensor, dict]:
-    """merbit_bicgstab (FP64): x with ||b - A x||_2 <= tol ||b||_2.  x: initial guess
-    (zeros if None), overwritten.  Returns (x, {iters, resid, status, converged, hist})."""
+    """merbit_bicgstab (FP64): x with ||b - A x||_2 <= tol ||b||_2.  vals None: every value
+    of the plan's matrix is 1 (no value stream).  x: initial guess (zeros if None),
+    overwritten.  Returns (x, {iters, resid, status, converged, hist})."""
     _need_cuda(vals, b, x)
-    if vals.dtype != torch.float64 or b.dtype != torch.float64:
+    if (vals is not None and vals.dtype != torch.float64) or b.dtype != torch.float64:
         raise ValueError("bicgstab takes f64 vals and b")
     if x is None:
         x = torch.zeros_like(b)

@@ -101,3 +101,19 @@ def test_bicgstab_edge_cases(cuda_device):
         assert not info["converged"] and info["status"] == 2 and info["iters"] == 6
         np.testing.assert_allclose(info["hist"], ref["resid"], rtol=1e-9)
         np.testing.assert_allclose(x, ref["x"], rtol=1e-9, atol=1e-12)
+
+
+def test_bicgstab_pattern_only_matches_unit_values(cuda_device):
+    """vals = NULL (all values 1, no value stream) runs the same recurrence as explicit
+    unit values."""
+    a = inputs.road_grid(50, 40, 0.6, 5)
+    xt = np.random.default_rng(6).uniform(-1, 1, a.n_rows)
+    b = oracle.spmv(a.row_ptr, a.col, a.val, xt)[0]
+    p = mb.plan(torch.from_numpy(a.row_ptr).cuda(), torch.from_numpy(a.col).cuda(), a.n_rows, a.n_cols)
+    bt = torch.from_numpy(b).cuda()
+    x1, i1 = mb.bicgstab(p, torch.from_numpy(a.val).cuda(), bt, tol=1e-30, max_iter=4)
+    x0, i0 = mb.bicgstab(p, None, bt, tol=1e-30, max_iter=4)
+    np.testing.assert_allclose(i0["hist"], i1["hist"], rtol=1e-12)
+    np.testing.assert_allclose(as_f64(x0), as_f64(x1), rtol=1e-11, atol=1e-13)
+    xc, ic = mb.bicgstab(p, None, bt)
+    assert ic["converged"] and _true_resid(a, b, as_f64(xc)) <= 1e-9
