@@ -609,7 +609,8 @@ def main():
                         "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": alg_bytes,
                         "bytes_per_nnz": alg_bytes / a.nnz, "parts": alg_parts,
-                        "kernel": "merbit_spmv_kernel<float,float,float,EpiPlain> + merbit_finalize_kernel",
+                        "kernel": "merbit_spmv_split_kernel<float,float,float,EpiPlain> (the default block "
+                                  "kernel for f32 values) + merbit_finalize_kernel",
                         "mean_launch_ms": mean_launch_ms,
                         "median_launch_ms": statistics.median(launch_ms)},
            "plan_ms": plan_ms, "gen_s": gen_s,

@@ -111,6 +111,26 @@ merbit_status merbit_plan_get_info(merbit_plan_t plan, merbit_plan_info* info);
 merbit_status merbit_plan_export(merbit_plan_t plan, uint32_t* tile_x, uint32_t* tile_y,
                                  uint32_t* lane_desc, int32_t* block_row);
 
+/* Block kernels of the product y = A x (every call that multiplies by a plan's
+ * matrix uses one of them; results agree to rounding):
+ *   MERBIT_KERNEL_CLASSIC: 256 threads per CTA; all of them gather x and form the
+ *     products of a block, then each warp reduces one tile (Sec. 4.2, one block at
+ *     a time per CTA, two copy stages).
+ *   MERBIT_KERNEL_SPLIT: 512 threads per CTA; 256 producer threads gather x and form
+ *     the products of the next blocks while the 256 consumer threads reduce and
+ *     commit the current one (three stages), so gathers and scans overlap.
+ *   MERBIT_KERNEL_AUTO (the default): the faster of the two for the value type, as
+ *     measured on sm_103a. */
+enum {
+  MERBIT_KERNEL_AUTO = 0,
+  MERBIT_KERNEL_CLASSIC = 1,
+  MERBIT_KERNEL_SPLIT = 2
+};
+
+/* Choose the block kernel for every later call on this plan (host-side setting,
+ * takes effect at the next launch).  Errors: EINVAL (NULL plan, unknown kernel). */
+merbit_status merbit_plan_set_kernel(merbit_plan_t plan, int kernel);
+
 /* Synchronise `stream` and report a kernel-side error of this plan's earlier
  * asynchronous calls (EDEVICE; the plan's device state is reset). */
 merbit_status merbit_plan_sync(merbit_plan_t plan, void* stream);

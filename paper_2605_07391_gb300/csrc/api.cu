@@ -413,6 +413,14 @@ merbit_status merbit_plan_export(merbit_plan_t p, uint32_t* tile_x, uint32_t* ti
   return MERBIT_OK;
 }
 
+merbit_status merbit_plan_set_kernel(merbit_plan_t p, int kernel) {
+  if (merbit_status s = check_plan(p)) return s;
+  if (kernel < MERBIT_KERNEL_AUTO || kernel > MERBIT_KERNEL_SPLIT)
+    return fail(MERBIT_EINVAL, "kernel must be MERBIT_KERNEL_AUTO, _CLASSIC or _SPLIT");
+  p->spmv_kernel = kernel;
+  return MERBIT_OK;
+}
+
 merbit_status merbit_plan_sync(merbit_plan_t p, void* stream) {
   if (merbit_status s = check_plan(p)) return s;
   cudaStream_t st = as_stream(stream);

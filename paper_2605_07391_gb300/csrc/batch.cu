@@ -398,6 +398,7 @@ struct merbit_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   merbit_dtype dt = MERBIT_F64;
+  int spmv_kernel = -1;
   const void* vals = nullptr;
   void* pi = nullptr;
   double alpha = -1.0, tol = -1.0;
@@ -624,7 +625,7 @@ merbit_status merbit_batch_pagerank(merbit_batch_t b, merbit_dtype dtype, const 
   const size_t es = dtype == MERBIT_F64 ? 8 : 4;
   cudaError_t e = cudaSuccess;
   const bool same = b->exec && b->dt == dtype && b->vals == vals && b->pi == pi && b->alpha == alpha &&
-                    b->tol == tol && b->max_iter == max_iter;
+                    b->tol == tol && b->max_iter == max_iter && b->spmv_kernel == b->plan->spmv_kernel;
   if (!same) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -655,6 +656,7 @@ merbit_status merbit_batch_pagerank(merbit_batch_t b, merbit_dtype dtype, const 
     b->alpha = alpha;
     b->tol = tol;
     b->max_iter = max_iter;
+    b->spmv_kernel = b->plan->spmv_kernel;
   }
   e = cudaGraphLaunch(b->exec, st);
   std::vector<int> conv((size_t)b->G);

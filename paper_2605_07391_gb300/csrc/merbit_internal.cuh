@@ -57,6 +57,7 @@ struct merbit_plan_s {
   int num_sms = 0;
   int64_t n_rows = 0, n_cols = 0, nnz = 0;
   int sigma = 14, tiles_per_block = merbit::kTilesPerBlock;
+  int spmv_kernel = 0;                   // MERBIT_KERNEL_AUTO / _CLASSIC / _SPLIT
   int64_t tile_num = 0, lane_num = 0, nb = 0;
   const int32_t* col = nullptr;          // borrowed
   uint32_t* tile_x = nullptr;

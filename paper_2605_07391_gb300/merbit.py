@@ -21,11 +21,13 @@ F32, F64, BF16, F16 = 0, 1, 2, 3
 PLAIN, IR_BF16, IR_F16, IR_F32 = 0, 1, 2, 3
 STATUS = {0: "OK", 1: "EINVAL", 2: "EOVERFLOW", 3: "ENOMEM", 4: "ECUDA", 5: "ENOTCONV",
           6: "EDEVICE"}
+KERNELS = {"auto": 0, "classic": 1, "split": 2}
 MODES = {"plain": PLAIN, "ir_bf16": IR_BF16, "ir_f16": IR_F16, "ir_f32": IR_F32}
 _TORCH_DT = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch.float16: F16}
 
 EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_get_info",
-           "merbit_plan_sync", "merbit_plan_export", "merbit_spmv", "merbit_spmv_ex", "merbit_spmm",
+           "merbit_plan_sync", "merbit_plan_set_kernel", "merbit_plan_export", "merbit_spmv",
+           "merbit_spmv_ex", "merbit_spmm",
            "merbit_ppr", "merbit_spmv_host", "merbit_spmv_host_async",
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
            "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
@@ -75,6 +77,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_plan_ex": [vp, vp, i64, i64, i64, i32, i32, vp, ctypes.POINTER(vp)],
             "merbit_plan_get_info": [vp, ctypes.POINTER(PlanInfo)],
             "merbit_plan_sync": [vp, vp],
+            "merbit_plan_set_kernel": [vp, ctypes.c_int],
             "merbit_plan_export": [vp, vp, vp, vp, vp],
             "merbit_spmv": [vp, i32, vp, vp, vp],
             "merbit_spmv_ex": [vp, i32, i32, vp, vp, vp, i32, vp],
@@ -206,6 +209,10 @@ class Plan:
                            (t.tile_x, t.tile_y, t.lane_desc, t.block_row))))
         return t
 
+    def set_kernel(self, kernel: str):
+        """Block kernel for later products: "auto", "classic" or "split"."""
+        _check("merbit_plan_set_kernel", load().merbit_plan_set_kernel(self.handle, KERNELS[kernel]))
+
     def sync(self, stream=None):
         _check("merbit_plan_sync", load().merbit_plan_sync(self.handle, _stream(stream)))
 
@@ -297,6 +304,12 @@ class Batch:
         if not self._handle:
             raise MerbitError("batch", 1, "batch was destroyed")
         return self._handle
+
+    def set_kernel(self, kernel: str):
+        """Block kernel of the batch's plan: "auto", "classic" or "split" (the solve is
+        recorded again at the next call)."""
+        h = ctypes.c_void_p(load().merbit_batch_get_plan(self.handle))
+        _check("merbit_plan_set_kernel", load().merbit_plan_set_kernel(h, KERNELS[kernel]))
 
     def plan_info(self) -> PlanInfo:
         """merbit_plan_get_info of the batch's plan (owned by the batch)."""
