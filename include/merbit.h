@@ -119,8 +119,9 @@ merbit_status merbit_plan_export(merbit_plan_t plan, uint32_t* tile_x, uint32_t*
  *   MERBIT_KERNEL_SPLIT: 512 threads per CTA; 256 producer threads gather x and form
  *     the products of the next blocks while the 256 consumer threads reduce and
  *     commit the current one (three stages), so gathers and scans overlap.
- *   MERBIT_KERNEL_AUTO (the default): the faster of the two for the value type, as
- *     measured on sm_103a. */
+ *   MERBIT_KERNEL_AUTO (the default): SPLIT for 32- and 64-bit values while two of
+ *     its CTAs fit on an SM (its three stages at the plan's sigma), else CLASSIC;
+ *     CLASSIC for 16-bit values (the faster choice in each case on sm_103a). */
 enum {
   MERBIT_KERNEL_AUTO = 0,
   MERBIT_KERNEL_CLASSIC = 1,

@@ -571,20 +571,23 @@ __global__ void __launch_bounds__(kThreads, 3)
 }
 
 // ---------------------------------------------------------------- warp-specialized kernel
-// The same block reduction with the x gather split off: kThreads consumer threads (warp
-// w reduces tile w of a block, as above) reduce and commit block i while kSplitProducers
-// producer threads gather x and form the products of blocks i + 1 and i + 2, so the SM's
+// The same block reduction with the x gather split off: kSplitConsumers consumer threads
+// (each warp reduces kTilesPerBlock / (kSplitConsumers / 32) tiles of a block with the
+// per-tile reduction above) reduce and commit block i while kSplitProducers producer
+// threads gather x and form the products of blocks i + 1 and i + 2, so the SM's
 // load path stays busy through the scans instead of in per-block bursts.  Three stages
 // rotate through bulk copy -> products -> reduction; block i + 3's copies are issued into
 // block i's stage once its consumers are done with it.  Producers hand a stage to the
 // consumers through a second mbarrier per stage (one arrival per producer warp).
+constexpr int kSplitConsumers = 256;
 constexpr int kSplitProducers = 256;
-constexpr int kSplitThreads = kThreads + kSplitProducers;
+constexpr int kSplitThreads = kSplitConsumers + kSplitProducers;
 constexpr int kSplitStages = 3;
+static_assert(kTilesPerBlock % (kSplitConsumers / 32) == 0, "whole tiles per consumer warp");
 
-// barrier 1 among the consumer threads only (warps 0 .. kThreads/32 - 1)
+// barrier 1 among the consumer threads only (warps 0 .. kSplitConsumers/32 - 1)
 __device__ __forceinline__ void consumers_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+  asm volatile("bar.sync 1, %0;" ::"n"(kSplitConsumers) : "memory");
 }
 __device__ __forceinline__ bool consumers_or(bool pred) {
   uint32_t r;
@@ -592,7 +595,7 @@ __device__ __forceinline__ bool consumers_or(bool pred) {
       "{\n\t.reg .pred q, o;\n\tsetp.ne.u32 q, %1, 0;\n\t"
       "bar.red.or.pred o, 1, %2, q;\n\tselp.u32 %0, 1, 0, o;\n\t}"
       : "=r"(r)
-      : "r"((uint32_t)pred), "n"(kThreads)
+      : "r"((uint32_t)pred), "n"(kSplitConsumers)
       : "memory");
   return r != 0;
 }
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
   __shared__ __align__(8) uint64_t full[S];    // the stage's bulk copies have landed
   __shared__ __align__(8) uint64_t ready[S];   // the stage's products are formed
   __shared__ StageInfo info[S];
-  __shared__ double red_smem[kThreads / 32][2];
+  __shared__ double red_smem[kSplitConsumers / 32][2];
   __shared__ int failed;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
 
@@ -687,10 +690,10 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
     }
   }
 
-  if (tid >= kThreads) {
+  if (tid >= kSplitConsumers) {
     // ---- producers: products val * x[col] of each block (load_smem), then the zeroed
     // row sums, in the stage the block was copied to
-    const int pt = tid - kThreads;
+    const int pt = tid - kSplitConsumers;
     for (int i = 0; i < nmine; ++i) {
       const int s = i % S;
       if (!mbar_wait_bounded(&full[s], (uint32_t)(i / S) & 1u)) {
@@ -743,15 +746,19 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       const int kb = blockIdx.x + i * G;
       const int v = blk(kb);
       const int s = i % S;
-      const int ti = v * kTilesPerBlock + warp;
-      const bool tile_ok = ti < g.tile_num;
-      uint32_t txs = 0, txe = 0, tys = 0, desc = 0;
-      const int j = ti * kOmega + lane;
-      if (tile_ok) {
-        txs = __ldg(g.tile_x + ti);
-        txe = __ldg(g.tile_x + ti + 1);
-        tys = __ldg(g.tile_y + ti);
-        if (!(tys & kMsb) && j < g.lane_num) desc = ld_stream(g.lane_desc + j, pol_stream);
+      constexpr int CW = kSplitConsumers / 32, TPW = kTilesPerBlock / CW;
+      uint32_t txs[TPW], txe[TPW], tys[TPW], desc[TPW];
+#pragma unroll
+      for (int t = 0; t < TPW; ++t) {
+        const int ti = v * kTilesPerBlock + warp + t * CW;
+        const int j = ti * kOmega + lane;
+        txs[t] = txe[t] = tys[t] = desc[t] = 0;
+        if (ti < g.tile_num) {
+          txs[t] = __ldg(g.tile_x + ti);
+          txe[t] = __ldg(g.tile_x + ti + 1);
+          tys[t] = __ldg(g.tile_y + ti);
+          if (!(tys[t] & kMsb) && j < g.lane_num) desc[t] = ld_stream(g.lane_desc + j, pol_stream);
+        }
       }
       int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
       const bool refill = (tid == 0) && (i + S < nmine);
@@ -769,14 +776,20 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       int pb;
       AT* prod = prod_of(s, in, pb);
       AT* s_y = prod + (in.x_be - pb);
-      if (tile_ok && txs < txe) {
-        const int y_ws = (int)(tys & ~kMsb);
-        reduce_tile<AT>(g, prod + ((int)txs - pb), s_y + (y_ws - in.y_bs), txs, txe, tys, y_ws,
-                        desc, j, lane);
+#pragma unroll
+      for (int t = 0; t < TPW; ++t) {
+        // a tile without products (or past the last tile) adds nothing
+        if (txs[t] < txe[t]) {
+          const int ti = v * kTilesPerBlock + warp + t * CW;
+          const int y_ws = (int)(tys[t] & ~kMsb);
+          reduce_tile<AT>(g, prod + ((int)txs[t] - pb), s_y + (y_ws - in.y_bs), txs[t], txe[t], tys[t],
+                          y_ws, desc[t], ti * kOmega + lane, lane);
+        }
       }
       consumers_sync();
 
-      for (int r = in.y_bs + 1 + tid; r < in.y_be; r += kThreads) epi.row(r, s_y[r - in.y_bs], p0, p1);
+      for (int r = in.y_bs + 1 + tid; r < in.y_be; r += kSplitConsumers)
+        epi.row(r, s_y[r - in.y_bs], p0, p1);
       if (tid == 0) atomicAdd(g.bnd_acc + __ldg(g.bnd_slot + v), static_cast<double>(s_y[0]));
       if (tid == 32 && in.y_be != in.y_bs && in.y_be < g.n_rows)
         atomicAdd(g.bnd_acc + __ldg(g.bnd_slot + v + 1), static_cast<double>(s_y[in.y_be - in.y_bs]));
@@ -798,7 +811,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       if (tid == 0) {
         double a = 0.0, b = 0.0;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) {
+        for (int w = 0; w < kSplitConsumers / 32; ++w) {
           a += red_smem[w][0];
           b += red_smem[w][1];
         }
@@ -879,35 +892,31 @@ __global__ void __launch_bounds__(256) merbit_finalize_kernel(const Geometry g, 
   }
 }
 
-// Which block kernel a launch uses: the plan's explicit choice, else the default.  Measured
-// on sm_103a (R-MAT scale 21 and 24, sigma 7 to 14): the split kernel is 15-30 % faster
-// for 32- and 64-bit values as long as its three stages leave room for two CTAs per SM,
-// and level with the classic kernel for 16-bit values, which keep the classic one.
-constexpr size_t kSplitSmemBudget = 200u * 1024u;   // two CTAs' stages per SM
-template <typename VT, typename AT>
-inline bool use_split_kernel(const merbit_plan_s* p) {
-  if (p->spmv_kernel == MERBIT_KERNEL_CLASSIC) return false;
-  if (p->spmv_kernel == MERBIT_KERNEL_SPLIT) return true;
-  if (sizeof(VT) < 4) return false;
-  return 2 * kSplitStages * stage_bytes<VT>(p->sigma) <= kSplitSmemBudget;
-}
-
 template <typename VT, typename XT, typename AT, typename Epi>
 cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, const Epi& epi,
                         cudaStream_t st) {
   if (p->nb == 0) return cudaSuccess;
+  // The split kernel is the default for 32- and 64-bit values while two of its CTAs fit
+  // on an SM (measured on sm_103a, R-MAT scale 21 and 24: 15-30 % faster than the classic
+  // kernel there, slower with one CTA per SM, level for 16-bit values).
   int grid = 0;
-  if (use_split_kernel<VT, AT>(p)) {
+  bool split = false;
+  if (p->spmv_kernel == MERBIT_KERNEL_SPLIT ||
+      (p->spmv_kernel == MERBIT_KERNEL_AUTO && sizeof(VT) >= 4)) {
     auto kern = merbit_spmv_split_kernel<VT, XT, AT, Epi>;
     const size_t smem = kSplitStages * stage_bytes<VT>(p->sigma);
     const size_t smem_max = kSplitStages * stage_bytes<VT>(kSigmaMax);
     grid = persistent_grid(reinterpret_cast<const void*>(kern), kSplitThreads, smem, smem_max,
                            p->num_sms);
-    if (grid <= 0) return cudaErrorInvalidConfiguration;
-    if ((int64_t)grid > p->nb) grid = (int)p->nb;
-    if (grid > kMaxParts) grid = kMaxParts;
-    kern<<<grid, kSplitThreads, smem, st>>>(p->geom(), vals, x, epi);
-  } else {
+    if (grid <= 0 && p->spmv_kernel == MERBIT_KERNEL_SPLIT) return cudaErrorInvalidConfiguration;
+    split = grid > 0 && (p->spmv_kernel == MERBIT_KERNEL_SPLIT || grid >= 2 * p->num_sms);
+    if (split) {
+      if ((int64_t)grid > p->nb) grid = (int)p->nb;
+      if (grid > kMaxParts) grid = kMaxParts;
+      kern<<<grid, kSplitThreads, smem, st>>>(p->geom(), vals, x, epi);
+    }
+  }
+  if (!split) {
     auto kern = merbit_spmv_kernel<VT, XT, AT, Epi>;
     const size_t smem = 2 * stage_bytes<VT>(p->sigma);
     const size_t smem_max = 2 * stage_bytes<VT>(kSigmaMax);
