@@ -386,9 +386,11 @@ def run_bicgstab(args, dev, stream) -> dict:
     for name, make in cases:
         a = make()
         n, nnz = a.n_rows, a.nnz
-        p = mb.plan(torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col).to(dev), n, n,
-                    stream=stream)
+        rp, col = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col).to(dev)
         vals = torch.from_numpy(a.val).to(dev)
+        # sigma for these FP64 products, by the autotuner (timed with the unit values read)
+        sigma, tune = mb.autotune_sigma(rp, col, vals, candidates=(14, 12, 10, 8), reps=3, stream=stream)
+        p = mb.plan(rp, col, n, n, sigma=sigma, stream=stream)
         xt = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, n)).to(dev)
         b = mb.spmv(p, vals, xt)
         mb.bicgstab(p, None, b, None, tol=1e-10, max_iter=3, stream=stream)        # warm
@@ -406,7 +408,8 @@ def run_bicgstab(args, dev, stream) -> dict:
         spmv_bytes = 4 * nnz + 8 * n + 8 * n + 8 * n + 4 * inf.lane_num + 8 * (inf.tile_num + 1)
         it_bytes = 2 * spmv_bytes + 8 * n * (4 + 3 + 7)
         it = max(1, info["iters"])
-        res[name] = {"n": n, "nnz": nnz, "iters": info["iters"], "status": info["status"],
+        res[name] = {"n": n, "nnz": nnz, "sigma": sigma, "autotune_ms_per_spmv": tune,
+                     "iters": info["iters"], "status": info["status"],
                      "rel_resid": info["resid"], "ms": ms, "ms_per_iter": ms / it,
                      "alg_bytes_per_iter": it_bytes, "alg_gbs": it_bytes * it / (ms * 1e-3) / 1e9,
                      "roofline_frac": it_bytes * it / (ms * 1e-3) / 1e9 / hbm,
