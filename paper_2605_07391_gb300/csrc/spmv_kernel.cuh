@@ -1,19 +1,24 @@
-// MERBIT SpMV kernel for sm_103a (Sec. 4.2: Algorithms MERBIT SpMV,
+// MERBIT SpMV kernels for sm_103a (Sec. 4.2: Algorithms MERBIT SpMV,
 // tile_normal_tackle, WarpSegmentedSum) with a pluggable row epilogue.
 //
 // Work unit: a block of W = 8 consecutive tiles (omega*sigma merge-path steps
 // each), one warp per tile, exactly as in the paper.  GB300-specific choices:
 //   * persistent CTAs (grid = SMs x resident CTAs) walk the blocks with a
-//     stride, with two shared-memory stages: while block v is reduced, the
-//     values and column indices of the CTA's next block are already in flight
-//     as two cp.async.bulk copies completing on an mbarrier (the block's
-//     nonzero range is contiguous, so one bulk copy per array suffices);
+//     stride; a block's values and column indices arrive in shared memory as
+//     two cp.async.bulk copies completing on an mbarrier, issued ahead of use
+//     (the block's nonzero range is contiguous, so one bulk copy per array
+//     suffices);
+//   * two block kernels share the stages and the per-tile reduction:
+//     merbit_spmv_kernel (all threads gather, then all reduce; two stages) and
+//     merbit_spmv_split_kernel (producer threads gather for the next blocks
+//     while consumer threads reduce the current one; three stages), which keeps
+//     the SM's gather path busy and is the default where two CTAs fit per SM;
 //   * matrix streams use an L2 evict_first policy, the x gather an
 //     evict_last policy (x is reused by every block and, in PageRank, by the
 //     next launch);
 //   * products overwrite the staged values (or column indices for 16-bit
 //     values) in place and the block's row partial sums follow them, so one
-//     stage holds W*omega*sigma + 16 elements of each array (Sec. 4.3's
+//     stage holds W*omega*sigma + 32 elements of each array (Sec. 4.3's
 //     (b+1)*sigma bound, re-derived for this layout);
 //   * rows shared between blocks (the block's first and last row) are added
 //     into per-row FP64 accumulators with fire-and-forget atomics; a small
@@ -322,6 +327,103 @@ struct ProdInVals {
   static constexpr bool value = sizeof(VT) == sizeof(AT);
 };
 
+// A block's coordinate range: nonzeros [xb, xe) and rows [yb, ye] (the tiles'
+// start coordinates of its first and one-past-last tile).
+struct BlockSpan {
+  int xb, xe;
+  uint32_t yb, ye;
+};
+
+// The shared-memory stages of a block kernel and the bulk copies that fill them.  Stage
+// s holds a block's values (none for UnitVal) and column indices; the products and the
+// block's row sums later overwrite them in place.
+template <typename VT, typename AT>
+struct Stages {
+  static constexpr int VE = 16 / (int)sizeof(VT);   // values per 16 bytes
+  const Geometry& g;
+  const VT* vals;
+  unsigned char* base;
+  size_t svb, stb;
+  int nnz_v, nnz_c;   // array ends rounded down to whole 16-byte units
+  uint64_t pol;       // L2 policy of the streams
+
+  __device__ __forceinline__ Stages(const Geometry& g_, const VT* v, unsigned char* smem, uint64_t p)
+      : g(g_), vals(v), base(smem), svb(stage_vals_bytes<VT>(g_.sigma)), stb(stage_bytes<VT>(g_.sigma)),
+        nnz_v(g_.nnz & ~(VE - 1)), nnz_c(g_.nnz & ~3), pol(p) {}
+
+  __device__ __forceinline__ VT* sv(int s) const { return reinterpret_cast<VT*>(base + (size_t)s * stb); }
+  __device__ __forceinline__ int32_t* sc(int s) const {
+    return reinterpret_cast<int32_t*>(base + (size_t)s * stb + svb);
+  }
+
+  __device__ __forceinline__ BlockSpan span(int v) const {
+    const int bs = v * kTilesPerBlock;
+    const int be = min(bs + kTilesPerBlock, g.tile_num);
+    return BlockSpan{(int)g.tile_x[bs], (int)g.tile_x[be], g.tile_y[bs] & ~kMsb, g.tile_y[be] & ~kMsb};
+  }
+
+  // Record the block's stage layout in *info and start its copies on bar (one thread).
+  __device__ __forceinline__ void issue(int s, const BlockSpan& b, StageInfo* info, uint64_t* bar) const {
+    StageInfo in;
+    in.x_bs = b.xb; in.x_be = b.xe; in.y_bs = (int)b.yb; in.y_be = (int)b.ye;
+    in.a0v = b.xb & ~(VE - 1);
+    in.endv = max(in.a0v, min((b.xe + VE - 1) & ~(VE - 1), nnz_v));
+    in.a0c = b.xb & ~3;
+    in.endc = max(in.a0c, min((b.xe + 3) & ~3, nnz_c));
+    *info = in;
+    const uint32_t bv = IsUnit<VT>::value ? 0u : (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT);
+    const uint32_t bc = (uint32_t)(in.endc - in.a0c) * 4u;
+    mbar_arrive_expect_tx(bar, bv + bc);
+    if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, bar, pol);
+    if (bc) bulk_g2s(sc(s), g.col + in.a0c, bc, bar, pol);
+  }
+
+  // The stage's product slots (over the values, or over the column indices for 16-bit
+  // values) and the nonzero index of slot 0.
+  __device__ __forceinline__ AT* prod(int s, const StageInfo& in, int& pb) const {
+    if constexpr (ProdInVals<VT, AT>::value) {
+      pb = in.a0v;
+      return reinterpret_cast<AT*>(sv(s));
+    } else {
+      pb = in.a0c;
+      return reinterpret_cast<AT*>(sc(s));
+    }
+  }
+
+  // product k - pb of a staged nonzero k: val * x[col] (x[col] for UnitVal)
+  template <typename XT>
+  __device__ __forceinline__ void gather(int s, const StageInfo& in, int k, const XT* x, uint64_t pol_x,
+                                         AT& xv) const {
+    const int c = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
+    xv = static_cast<AT>(ld_x(x + c, pol_x));
+  }
+  __device__ __forceinline__ AT product(int s, const StageInfo& in, int k, AT xv) const {
+    if constexpr (IsUnit<VT>::value) {
+      return xv;
+    } else {
+      return static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k])) * xv;
+    }
+  }
+};
+
+// The blocks a CTA walks: all blocks in order, or the epilogue's list (*block_count
+// entries, read at kernel start).
+template <typename Epi>
+struct BlockOrder {
+  int n;
+  const int* list = nullptr;
+  __device__ __forceinline__ BlockOrder(const Geometry& g, const Epi& epi) : n(g.nb) {
+    if constexpr (HasBlockList<Epi>::value) {
+      n = *reinterpret_cast<const volatile int*>(epi.block_count);
+      list = epi.block_list;
+    }
+  }
+  __device__ __forceinline__ int operator()(int k) const {
+    if constexpr (HasBlockList<Epi>::value) return __ldg(list + k);
+    else return k;
+  }
+};
+
 // One warp reduces one tile of a staged block into the block's row sums (Algorithm
 // tile_normal_tackle with WarpSegmentedSum; tile_fast_tackle for a tile marked as part
 // of a single row).  pt: the tile's first product; sy: the row sums from the tile's first
@@ -390,7 +492,6 @@ __global__ void __launch_bounds__(kThreads, 3)
     merbit_spmv_kernel(const Geometry g, const VT* __restrict__ vals, const XT* __restrict__ x,
                        Epi epi) {
   static_assert(ProdInVals<VT, AT>::value || sizeof(AT) == 4, "product slot width");
-  constexpr int VE = 16 / (int)sizeof(VT);   // values per 16 bytes
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ StageInfo info[2];
   __shared__ double red_smem[kThreads / 32][2];
@@ -403,47 +504,11 @@ __global__ void __launch_bounds__(kThreads, 3)
   if (epi.skip(g.red)) return;
   epi.init();
 
-  const size_t svb = stage_vals_bytes<VT>(g.sigma);
-  const size_t stb = stage_bytes<VT>(g.sigma);
-  auto sv = [&](int s) { return reinterpret_cast<VT*>(dyn_smem + (size_t)s * stb); };
-  auto sc = [&](int s) { return reinterpret_cast<int32_t*>(dyn_smem + (size_t)s * stb + svb); };
-
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_x = policy_evict_last();
-  const int nnz_v = g.nnz & ~(VE - 1);
-  const int nnz_c = g.nnz & ~3;
-
-  // geometry of block v, as needed to issue its copies (thread 0 only)
-  auto geom_of = [&](int v, int& xb, int& xe, uint32_t& yb, uint32_t& ye) {
-    const int bs = v * kTilesPerBlock;
-    const int be = min(bs + kTilesPerBlock, g.tile_num);
-    xb = (int)g.tile_x[bs];
-    xe = (int)g.tile_x[be];
-    yb = g.tile_y[bs] & ~kMsb;
-    ye = g.tile_y[be] & ~kMsb;
-  };
-  auto issue = [&](int s, int xb, int xe, uint32_t yb, uint32_t ye) {
-    StageInfo in;
-    in.x_bs = xb; in.x_be = xe; in.y_bs = (int)yb; in.y_be = (int)ye;
-    in.a0v = xb & ~(VE - 1);
-    in.endv = max(in.a0v, min((xe + VE - 1) & ~(VE - 1), nnz_v));
-    in.a0c = xb & ~3;
-    in.endc = max(in.a0c, min((xe + 3) & ~3, nnz_c));
-    info[s] = in;
-    const uint32_t bv = IsUnit<VT>::value ? 0u : (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT);
-    const uint32_t bc = (uint32_t)(in.endc - in.a0c) * 4u;
-    mbar_arrive_expect_tx(&mbar[s], bv + bc);
-    if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, &mbar[s], pol_stream);
-    if (bc) bulk_g2s(sc(s), g.col + in.a0c, bc, &mbar[s], pol_stream);
-  };
-
-  // the k-th block to process: all blocks in order, or the epilogue's list
-  int nbl = g.nb;
-  if constexpr (HasBlockList<Epi>::value) nbl = *reinterpret_cast<const volatile int*>(epi.block_count);
-  auto blk = [&](int k) -> int {
-    if constexpr (HasBlockList<Epi>::value) return __ldg(epi.block_list + k);
-    else return k;
-  };
+  const Stages<VT, AT> st(g, vals, dyn_smem, pol_stream);
+  const BlockOrder<Epi> blk(g, epi);
+  const int nbl = blk.n;
 
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
@@ -452,9 +517,8 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
   __syncthreads();
   if (tid == 0) {
-    int xb, xe; uint32_t yb, ye;
-    if (blockIdx.x < nbl) { geom_of(blk(blockIdx.x), xb, xe, yb, ye); issue(0, xb, xe, yb, ye); }
-    if (blockIdx.x + G < nbl) { geom_of(blk(blockIdx.x + G), xb, xe, yb, ye); issue(1, xb, xe, yb, ye); }
+    if (blockIdx.x < nbl) st.issue(0, st.span(blk(blockIdx.x)), &info[0], &mbar[0]);
+    if (blockIdx.x + G < nbl) st.issue(1, st.span(blk(blockIdx.x + G)), &info[1], &mbar[1]);
   }
 
   double p0 = 0.0, p1 = 0.0;
@@ -476,9 +540,9 @@ __global__ void __launch_bounds__(kThreads, 3)
       if (!(tys & kMsb) && j < g.lane_num) desc = ld_stream(g.lane_desc + j, pol_stream);
     }
     // geometry for the copy issued at the end of this iteration
-    int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
+    BlockSpan next{0, 0, 0u, 0u};
     const bool refill = (tid == 0) && (kb + 2 * G < nbl);
-    if (refill) geom_of(blk(kb + 2 * G), nxb, nxe, nyb, nye);
+    if (refill) next = st.span(blk(kb + 2 * G));
 
     const bool ok = mbar_wait_bounded(&mbar[s], par);
     if (__syncthreads_or(!ok)) {
@@ -489,15 +553,8 @@ __global__ void __launch_bounds__(kThreads, 3)
       return;
     }
     const StageInfo in = info[s];
-    AT* prod;
     int pb;
-    if constexpr (ProdInVals<VT, AT>::value) {
-      prod = reinterpret_cast<AT*>(sv(s));
-      pb = in.a0v;
-    } else {
-      prod = reinterpret_cast<AT*>(sc(s));
-      pb = in.a0c;
-    }
+    AT* prod = st.prod(s, in, pb);
 
     // ---- stage products val * x[col] (load_smem of Algorithm MERBIT SpMV)
     {
@@ -507,24 +564,12 @@ __global__ void __launch_bounds__(kThreads, 3)
       for (int u = 0; u < kSigmaMax; ++u) {
         const int e = tid + u * kThreads;
         xv[u] = AT(0);
-        if (e < cnt) {
-          const int k = in.x_bs + e;
-          const int c = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
-          xv[u] = static_cast<AT>(ld_x(x + c, pol_x));
-        }
+        if (e < cnt) st.gather(s, in, in.x_bs + e, x, pol_x, xv[u]);
       }
 #pragma unroll
       for (int u = 0; u < kSigmaMax; ++u) {
         const int e = tid + u * kThreads;
-        if (e < cnt) {
-          const int k = in.x_bs + e;
-          if constexpr (IsUnit<VT>::value) {
-            prod[k - pb] = xv[u];
-          } else {
-            const AT v = static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
-            prod[k - pb] = v * xv[u];
-          }
-        }
+        if (e < cnt) prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
       }
     }
     AT* s_y = prod + (in.x_be - pb);
@@ -547,7 +592,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     // stage s is free again once every thread is past this point
     fence_proxy_async_smem();
     __syncthreads();
-    if (refill) issue(s, nxb, nxe, nyb, nye);
+    if (refill) st.issue(s, next, &info[s], &mbar[s]);
   }
 
   if constexpr (Epi::kReduce) {
@@ -605,7 +650,6 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
     merbit_spmv_split_kernel(const Geometry g, const VT* __restrict__ vals, const XT* __restrict__ x,
                           Epi epi) {
   static_assert(ProdInVals<VT, AT>::value || sizeof(AT) == 4, "product slot width");
-  constexpr int VE = 16 / (int)sizeof(VT);
   constexpr int S = kSplitStages;
   __shared__ __align__(8) uint64_t full[S];    // the stage's bulk copies have landed
   __shared__ __align__(8) uint64_t ready[S];   // the stage's products are formed
@@ -621,56 +665,13 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
   if (epi.skip(g.red)) return;
   epi.init();
 
-  const size_t svb = stage_vals_bytes<VT>(g.sigma);
-  const size_t stb = stage_bytes<VT>(g.sigma);
-  auto sv = [&](int s) { return reinterpret_cast<VT*>(dyn_smem + (size_t)s * stb); };
-  auto sc = [&](int s) { return reinterpret_cast<int32_t*>(dyn_smem + (size_t)s * stb + svb); };
-
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_x = policy_evict_last();
-  const int nnz_v = g.nnz & ~(VE - 1);
-  const int nnz_c = g.nnz & ~3;
-
-  auto geom_of = [&](int v, int& xb, int& xe, uint32_t& yb, uint32_t& ye) {
-    const int bs = v * kTilesPerBlock;
-    const int be = min(bs + kTilesPerBlock, g.tile_num);
-    xb = (int)g.tile_x[bs];
-    xe = (int)g.tile_x[be];
-    yb = g.tile_y[bs] & ~kMsb;
-    ye = g.tile_y[be] & ~kMsb;
-  };
-  auto issue = [&](int s, int xb, int xe, uint32_t yb, uint32_t ye) {
-    StageInfo in;
-    in.x_bs = xb; in.x_be = xe; in.y_bs = (int)yb; in.y_be = (int)ye;
-    in.a0v = xb & ~(VE - 1);
-    in.endv = max(in.a0v, min((xe + VE - 1) & ~(VE - 1), nnz_v));
-    in.a0c = xb & ~3;
-    in.endc = max(in.a0c, min((xe + 3) & ~3, nnz_c));
-    info[s] = in;
-    const uint32_t bv = IsUnit<VT>::value ? 0u : (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT);
-    const uint32_t bc = (uint32_t)(in.endc - in.a0c) * 4u;
-    mbar_arrive_expect_tx(&full[s], bv + bc);
-    if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, &full[s], pol_stream);
-    if (bc) bulk_g2s(sc(s), g.col + in.a0c, bc, &full[s], pol_stream);
-  };
-
-  int nbl = g.nb;
-  if constexpr (HasBlockList<Epi>::value) nbl = *reinterpret_cast<const volatile int*>(epi.block_count);
-  auto blk = [&](int k) -> int {
-    if constexpr (HasBlockList<Epi>::value) return __ldg(epi.block_list + k);
-    else return k;
-  };
+  const Stages<VT, AT> st(g, vals, dyn_smem, pol_stream);
+  const BlockOrder<Epi> blk(g, epi);
+  const int nbl = blk.n;
   // this CTA's blocks: blk(blockIdx.x + i * G) for i < nmine
   const int nmine = (int)blockIdx.x < nbl ? (nbl - 1 - (int)blockIdx.x) / G + 1 : 0;
-  auto prod_of = [&](int s, const StageInfo& in, int& pb) -> AT* {
-    if constexpr (ProdInVals<VT, AT>::value) {
-      pb = in.a0v;
-      return reinterpret_cast<AT*>(sv(s));
-    } else {
-      pb = in.a0c;
-      return reinterpret_cast<AT*>(sc(s));
-    }
-  };
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -683,11 +684,8 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
   __syncthreads();
   int issued = 0;   // blocks whose copies thread 0 has issued
   if (tid == 0) {
-    for (; issued < S && issued < nmine; ++issued) {
-      int xb, xe; uint32_t yb, ye;
-      geom_of(blk(blockIdx.x + issued * G), xb, xe, yb, ye);
-      issue(issued, xb, xe, yb, ye);
-    }
+    for (; issued < S && issued < nmine; ++issued)
+      st.issue(issued, st.span(blk(blockIdx.x + issued * G)), &info[issued], &full[issued]);
   }
 
   if (tid >= kSplitConsumers) {
@@ -703,7 +701,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       }
       const StageInfo in = info[s];
       int pb;
-      AT* prod = prod_of(s, in, pb);
+      AT* prod = st.prod(s, in, pb);
       const int cnt = in.x_be - in.x_bs;
       for (int base = 0; base < cnt; base += kSplitProducers * kSigmaMax) {
         AT xv[kSigmaMax];
@@ -711,24 +709,12 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
         for (int u = 0; u < kSigmaMax; ++u) {
           const int e = base + pt + u * kSplitProducers;
           xv[u] = AT(0);
-          if (e < cnt) {
-            const int k = in.x_bs + e;
-            const int c = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
-            xv[u] = static_cast<AT>(ld_x(x + c, pol_x));
-          }
+          if (e < cnt) st.gather(s, in, in.x_bs + e, x, pol_x, xv[u]);
         }
 #pragma unroll
         for (int u = 0; u < kSigmaMax; ++u) {
           const int e = base + pt + u * kSplitProducers;
-          if (e < cnt) {
-            const int k = in.x_bs + e;
-            if constexpr (IsUnit<VT>::value) {
-              prod[k - pb] = xv[u];
-            } else {
-              const AT v = static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
-              prod[k - pb] = v * xv[u];
-            }
-          }
+          if (e < cnt) prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
         }
       }
       AT* s_y = prod + (in.x_be - pb);
@@ -760,9 +746,9 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
           if (!(tys[t] & kMsb) && j < g.lane_num) desc[t] = ld_stream(g.lane_desc + j, pol_stream);
         }
       }
-      int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
+      BlockSpan next{0, 0, 0u, 0u};
       const bool refill = (tid == 0) && (i + S < nmine);
-      if (refill) geom_of(blk(kb + S * G), nxb, nxe, nyb, nye);
+      if (refill) next = st.span(blk(kb + S * G));
 
       const bool ok = mbar_wait_bounded(&ready[s], (uint32_t)(i / S) & 1u);
       if (consumers_or(!ok)) {
@@ -774,7 +760,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       }
       const StageInfo in = info[s];
       int pb;
-      AT* prod = prod_of(s, in, pb);
+      AT* prod = st.prod(s, in, pb);
       AT* s_y = prod + (in.x_be - pb);
 #pragma unroll
       for (int t = 0; t < TPW; ++t) {
@@ -796,7 +782,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       fence_proxy_async_smem();
       consumers_sync();
       if (refill) {
-        issue(s, nxb, nxe, nyb, nye);
+        st.issue(s, next, &info[s], &full[s]);
         ++issued;
       }
     }
