@@ -703,16 +703,19 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       int pb;
       AT* prod = st.prod(s, in, pb);
       const int cnt = in.x_be - in.x_bs;
-      for (int base = 0; base < cnt; base += kSplitProducers * kSigmaMax) {
-        AT xv[kSigmaMax];
+      // gathers in flight per thread: up to 14 (one block at sigma 14); 10 for 8-byte
+      // products, which keeps them in registers (one block at sigma <= 10)
+      constexpr int NB = sizeof(AT) == 8 ? 10 : kSigmaMax;
+      for (int base = 0; base < cnt; base += kSplitProducers * NB) {
+        AT xv[NB];
 #pragma unroll
-        for (int u = 0; u < kSigmaMax; ++u) {
+        for (int u = 0; u < NB; ++u) {
           const int e = base + pt + u * kSplitProducers;
           xv[u] = AT(0);
           if (e < cnt) st.gather(s, in, in.x_bs + e, x, pol_x, xv[u]);
         }
 #pragma unroll
-        for (int u = 0; u < kSigmaMax; ++u) {
+        for (int u = 0; u < NB; ++u) {
           const int e = base + pt + u * kSplitProducers;
           if (e < cnt) prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
         }
