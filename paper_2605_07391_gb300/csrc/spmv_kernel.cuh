@@ -694,9 +694,13 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
     const int pt = tid - kSplitConsumers;
     for (int i = 0; i < nmine; ++i) {
       const int s = i % S;
-      if (!mbar_wait_bounded(&full[s], (uint32_t)(i / S) & 1u)) {
-        atomicOr(&g.red->err, 1);
-        failed = 1;
+      // a warp gives up as a whole, so none of its lanes is left at the __syncwarp below
+      const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(i / S) & 1u);
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) {
+          atomicOr(&g.red->err, 1);
+          failed = 1;
+        }
         break;
       }
       const StageInfo in = info[s];
