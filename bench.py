@@ -4,9 +4,11 @@ Workload: the R-MAT scale-24 transition matrix P^T (16,777,216 vertices, edge
 factor 16, a/b/c/d = .57/.19/.19/.05, seed 7, self loops and duplicates
 dropped), synthetic.  One timed step is one FP32 SpMV y = P^T x through the
 plan (built once, outside the timed region, its time reported as plan_ms);
-x ~ U[0,1).  The same run then times PageRank to L1 residual 1e-10 in every
-precision mode, the SpMV through host buffers (e2e) and the CPU oracle on a
-bounded sample (cpu_baseline).
+x ~ U[0,1).  The same run then times the product with FP64 values (on the sigma the
+autotuner picks for them) and bf16 values, PageRank to L1 residual 1e-10 in every
+precision mode, the SpMV through host buffers (e2e), the batched, many-graph,
+BiCGSTAB and differentiation workloads, and the CPU oracle on a bounded sample
+(cpu_baseline).
 
 Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle
 instead (the reference arm of this project is the float64 oracle).
