@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SpMV Gnnz/s + % HBM roofline; PageRank time to 1e-10, mixed vs plain FP32"
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the roofline's peak is the measured copy rate)
 WORKLOADS = {
     # name: (scale, edge_factor, seed)
     "rmat24_transition": (24, 16, 7),
@@ -612,6 +613,8 @@ def main():
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved / hbm_peak, "traffic": traffic,
                         "peak_kind": peak_kind,
+                        "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                        "traffic_bytes_per_nnz": traffic / a.nnz if traffic else None,
                         "algorithmic_bytes_per_launch": alg_bytes,
                         "bytes_per_nnz": alg_bytes / a.nnz, "parts": alg_parts,
                         "kernel": "merbit_spmv_split_kernel<float,float,float,EpiPlain> (the default block "
