@@ -51,4 +51,5 @@ def test_errors_without_device_work():
     assert st == 2
     assert lib.merbit_spmv(None, 0, None, None, None) == 1
     assert lib.merbit_pagerank(None, 0, None, 0.85, 1e-10, None) == 1
+    assert lib.merbit_plan_set_kernel(None, 2) == 1 and b"plan" in lib.merbit_last_error()
     lib.merbit_plan_destroy(None)
