@@ -66,6 +66,13 @@ cudaError_t get_state(const merbit_plan_s* p, size_t xb, size_t yb, AsyncState**
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a->kernel_done[s], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a->copy_done[s], cudaEventDisableTiming);
     }
+    if (e != cudaSuccess) {
+      // keep no half-built state: the next call starts over
+      free_state(a);
+      g_state.erase(p);
+      *out = nullptr;
+      return e;
+    }
   }
   if (e == cudaSuccess && (a->xb < xb || a->yb < yb)) {
     // resize only when nothing is pending on the slots
