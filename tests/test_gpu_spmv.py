@@ -240,3 +240,31 @@ def test_spmv_plans_of_different_sigma_interleaved(cuda_device, dtype):
     a = inputs.rmat_uniform(13, 16, 5, 5)
     for sigma in (7, 14, 1, 14, 7):
         _run(a, dtype, sigma=sigma)
+
+
+def test_spmv_full_rmat24_bench_configuration(cuda_device):
+    """The product bench.py times, at full size: R-MAT scale 24 transition matrix, x ~ U[0,1)
+    (seed 2), plan reused over 3 calls.  f32 on the sigma-14 plan (the split kernel) and
+    f64 on the sigma-14 (classic kernel) and sigma-10 (split kernel) plans: sampled rows
+    against the oracle, the column-sum identity, and exact zeros in empty rows."""
+    a = inputs.rmat_transition(24, 16, 7)
+    rows = _sample_rows(a)
+    x64 = inputs.uniform_vector(a.n_cols, 2)
+    empty = np.diff(a.row_ptr) == 0
+    for dtype, sigma in ((torch.float32, 14), (torch.float64, 14), (torch.float64, 10)):
+        p, _ = make_plan(a, sigma)
+        vals = torch.from_numpy(a.val).to("cuda", dtype)
+        x = torch.from_numpy(x64).to("cuda", dtype)
+        y = torch.empty(a.n_rows, dtype=dtype, device="cuda")
+        for _ in range(3):
+            mb.spmv(p, vals, x, y)
+        p.sync()
+        yh = as_f64(y)
+        y_ref, d = oracle.spmv_rows(a.row_ptr, a.col, as_f64(vals), as_f64(x), rows)
+        check_rel(yh[rows], y_ref, d, TOL[dtype], f"rmat24 {dtype} sigma={sigma}")
+        colsum = np.bincount(a.col, weights=as_f64(vals), minlength=a.n_cols)
+        tot = float(np.dot(colsum, as_f64(x)))
+        assert abs(float(yh.sum()) - tot) <= 1e-5 * tot
+        assert np.count_nonzero(yh[empty]) == 0
+        p.destroy()
+        del vals, x, y
