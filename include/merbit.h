@@ -413,19 +413,38 @@ merbit_status merbit_pagerank_ex(merbit_plan_t plan, merbit_dtype dtype, const v
  * schedule (sigma = 14) and runs the product without allocating anything: it
  * uses the caller's row_ptr, col_idx, vals, x (n_cols entries) and y (n_rows
  * entries, fully overwritten), all device pointers, plus a fixed scratch array
- * compiled into the library (8 MiB; every GPU that loads the library keeps it
- * until the process exits).  That is enough for matrices of up to about 27
- * million rows plus nonzeros; larger ones are rejected with MERBIT_EINVAL and
- * a message from merbit_last_error() (use merbit_plan / merbit_spmv).  The
- * first call on a device looks up the scratch array's device address; make
- * that first call before any stream capture.  All calls share the one array:
- * calls that overlap on the GPU (other streams, other threads) race and give
- * wrong results.  Asynchronous on `stream`; vals and col_idx must be 16-byte
- * aligned; row_ptr is trusted (not checked).  Errors: EINVAL, EOVERFLOW, ECUDA.
+ * compiled into the library (8 MiB = 8,388,608 bytes; every GPU that loads
+ * the library keeps it until the process exits).  A matrix needs
+ *     66,816 + up256(4 lane_num) + 2 up256(4 (tile_num + 1))
+ *            + 2 up256(4 (block_num + 1)) + up256(8 (block_num + 1))
+ * bytes of it, with S = n_rows + nnz, lane_num = ceil(S / 14),
+ * tile_num = ceil(S / 448), block_num = ceil(tile_num / 8) and up256 rounding
+ * up to a multiple of 256: about 27 million rows plus nonzeros at most.
+ * Larger matrices are rejected with MERBIT_EINVAL and a message from
+ * merbit_last_error() (use merbit_plan / merbit_spmv).  Every call looks up the
+ * scratch array's device address in the current context; make the first call
+ * on a device before any stream capture (the lookup may load the module).
+ * All calls share the one array: calls that overlap on the GPU (other streams,
+ * other threads) race and give wrong results.  Asynchronous on `stream`; vals
+ * and col_idx must be 16-byte aligned, x and y 4-byte aligned; row_ptr is
+ * trusted (not checked).  Errors: EINVAL, EOVERFLOW, ECUDA.  A kernel that
+ * gives up on a bounded wait cannot report it through this asynchronous call:
+ * it sets an error word in the scratch array, which stays set until
+ * merbit_spmv_noalloc_status reads it.  Callers must check that status before
+ * trusting y.
  */
 merbit_status merbit_spmv_noalloc(const int32_t* row_ptr, const int32_t* col_idx, const float* vals,
                                   const float* x, float* y, int64_t n_rows, int64_t n_cols,
                                   int64_t nnz, void* stream);
+
+/*
+ * merbit_spmv_noalloc_status — synchronises `stream` and reports whether any
+ * merbit_spmv_noalloc call since the last status query had a kernel give up on
+ * a bounded wait (then the y of that call is incomplete): MERBIT_EDEVICE, with
+ * the error word cleared, or MERBIT_OK.  Allocates nothing (a 4-byte copy into
+ * a host variable).  No counterpart in the paper.  Errors: EDEVICE, ECUDA.
+ */
+merbit_status merbit_spmv_noalloc_status(void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* merbit_last_error(void);

@@ -11,7 +11,6 @@
 // kNoAllocScratchBytes; every GPU that loads the library keeps it until the
 // process exits.
 #include <cstdio>
-#include <mutex>
 
 #include "merbit_internal.cuh"
 
@@ -25,29 +24,42 @@ using namespace merbit;
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;   // 8 MiB per device
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Device address of the scratch array, looked up once per device with that
-// device current.  In host code the array's name is only a host-side handle,
-// so the kernels must receive this address instead.
-cudaError_t scratch_address(int dev, void** out) {
-  static std::mutex mu;
-  static void* addr[kMaxDevices] = {};
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    addr[dev] = p;
-  }
-  *out = addr[dev];
-  return cudaSuccess;
+// Device address of the scratch array in the current device's context, looked
+// up on every call (a host-side lookup, no allocation).  In host code the
+// array's name is only a host-side handle, so the kernels must receive this
+// address instead.  Looking it up each time keeps it right after a
+// cudaDeviceReset or under another context on the same device.
+cudaError_t scratch_address(void** out) {
+  return cudaGetSymbolAddress(out, g_noalloc_scratch);
 }
+
+// Bytes of scratch a matrix needs (the carve order of merbit_spmv_noalloc).
+struct Carve {
+  size_t off[9];
+};
+
+Carve carve(const merbit_plan_s& p) {
+  Carve c;
+  c.off[0] = 0;
+  c.off[1] = c.off[0] + up256(sizeof(RedState));
+  c.off[2] = c.off[1] + up256(sizeof(double2) * kMaxParts);
+  c.off[3] = c.off[2] + up256(sizeof(uint32_t) * (size_t)(p.tile_num + 1));
+  c.off[4] = c.off[3] + up256(sizeof(uint32_t) * (size_t)(p.tile_num + 1));
+  c.off[5] = c.off[4] + up256(sizeof(uint32_t) * (size_t)p.lane_num);
+  c.off[6] = c.off[5] + up256(sizeof(int32_t) * (size_t)(p.nb + 1));
+  c.off[7] = c.off[6] + up256(sizeof(int32_t) * (size_t)(p.nb + 1));
+  c.off[8] = c.off[7] + up256(sizeof(double) * (size_t)(p.nb + 1));
+  return c;
+}
+
+// The header documents the fixed part of the requirement as 66,816 bytes.
+static_assert(((sizeof(RedState) + 255) & ~size_t(255)) + sizeof(double2) * kMaxParts == 66816,
+              "fixed scratch part changed: update merbit.h");
 
 merbit_status noalloc_fail(merbit_status s, const char* msg) {
   set_last_error(msg);
@@ -69,7 +81,8 @@ merbit_status merbit_spmv_noalloc(const int32_t* row_ptr, const int32_t* col_idx
     return noalloc_fail(MERBIT_EOVERFLOW, "n_rows + nnz does not fit the int32 merge path");
   if (nnz > 0 && ((reinterpret_cast<uintptr_t>(vals) | reinterpret_cast<uintptr_t>(col_idx)) & 15))
     return noalloc_fail(MERBIT_EINVAL, "vals and col_idx must be 16-byte aligned");
-  if (n_rows == 0) return MERBIT_OK;
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 3)
+    return noalloc_fail(MERBIT_EINVAL, "x and y must be 4-byte aligned");
 
   // schedule sizes for sigma = 14 (Sec. 4.1.1 counts)
   merbit_plan_s p;
@@ -85,24 +98,16 @@ merbit_status merbit_spmv_noalloc(const int32_t* row_ptr, const int32_t* col_idx
   p.nb = (p.tile_num + kTilesPerBlock - 1) / kTilesPerBlock;
 
   // carve the scratch: state | partials | tile_x | tile_y | lane_desc | rows | slots | FP64 accumulators
-  size_t off[9];
-  off[0] = 0;
-  off[1] = off[0] + up256(sizeof(RedState));
-  off[2] = off[1] + up256(sizeof(double2) * kMaxParts);
-  off[3] = off[2] + up256(sizeof(uint32_t) * (size_t)(p.tile_num + 1));
-  off[4] = off[3] + up256(sizeof(uint32_t) * (size_t)(p.tile_num + 1));
-  off[5] = off[4] + up256(sizeof(uint32_t) * (size_t)p.lane_num);
-  off[6] = off[5] + up256(sizeof(int32_t) * (size_t)(p.nb + 1));
-  off[7] = off[6] + up256(sizeof(int32_t) * (size_t)(p.nb + 1));
-  off[8] = off[7] + up256(sizeof(double) * (size_t)(p.nb + 1));
-  if (off[8] > kNoAllocScratchBytes) {
+  const Carve c = carve(p);
+  if (c.off[8] > kNoAllocScratchBytes) {
     char msg[256];
     std::snprintf(msg, sizeof(msg),
                   "matrix too large for merbit_spmv_noalloc: it needs %zu bytes of scratch and "
                   "the library reserves %zu; use merbit_plan / merbit_spmv instead",
-                  off[8], kNoAllocScratchBytes);
+                  c.off[8], kNoAllocScratchBytes);
     return noalloc_fail(MERBIT_EINVAL, msg);
   }
+  if (n_rows == 0) return MERBIT_OK;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(MERBIT_ECUDA, "cudaGetDevice failed");
@@ -110,26 +115,52 @@ merbit_status merbit_spmv_noalloc(const int32_t* row_ptr, const int32_t* col_idx
     return noalloc_fail(MERBIT_ECUDA, "cudaDeviceGetAttribute failed");
   p.device = dev;
   void* base = nullptr;
-  if (cudaError_t e = scratch_address(dev, &base); e != cudaSuccess)
+  if (cudaError_t e = scratch_address(&base); e != cudaSuccess)
     return noalloc_fail(MERBIT_ECUDA, cudaGetErrorString(e));
   unsigned char* b = static_cast<unsigned char*>(base);
-  p.red = reinterpret_cast<RedState*>(b + off[0]);
-  p.part = reinterpret_cast<double2*>(b + off[1]);
-  p.tile_x = reinterpret_cast<uint32_t*>(b + off[2]);
-  p.tile_y = reinterpret_cast<uint32_t*>(b + off[3]);
-  p.lane_desc = reinterpret_cast<uint32_t*>(b + off[4]);
-  p.bnd_row = reinterpret_cast<int32_t*>(b + off[5]);
-  p.bnd_slot = reinterpret_cast<int32_t*>(b + off[6]);
-  p.bnd_acc = reinterpret_cast<double*>(b + off[7]);
+  p.red = reinterpret_cast<RedState*>(b + c.off[0]);
+  p.part = reinterpret_cast<double2*>(b + c.off[1]);
+  p.tile_x = reinterpret_cast<uint32_t*>(b + c.off[2]);
+  p.tile_y = reinterpret_cast<uint32_t*>(b + c.off[3]);
+  p.lane_desc = reinterpret_cast<uint32_t*>(b + c.off[4]);
+  p.bnd_row = reinterpret_cast<int32_t*>(b + c.off[5]);
+  p.bnd_slot = reinterpret_cast<int32_t*>(b + c.off[6]);
+  p.bnd_acc = reinterpret_cast<double*>(b + c.off[7]);
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // the array keeps the previous call's contents: the error word and the
-  // boundary accumulators must start at zero
-  cudaError_t e = cudaMemsetAsync(p.red, 0, sizeof(RedState), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p.bnd_acc, 0, sizeof(double) * (size_t)(p.nb + 1), st);
+  // The array keeps the previous call's contents.  The boundary accumulators
+  // must start at zero (a call whose kernel gave up may have left some set).
+  // The error word at the start of the array is left alone: it is zero when
+  // the library loads, a kernel that gives up on a bounded wait sets it, and
+  // only merbit_spmv_noalloc_status reads and clears it.
+  cudaError_t e = cudaMemsetAsync(p.bnd_acc, 0, sizeof(double) * (size_t)(p.nb + 1), st);
   if (e == cudaSuccess) e = build_tiles(&p, row_ptr, st);
   if (e == cudaSuccess) e = spmv_plain_f32(&p, vals, x, y, st);
   if (e != cudaSuccess) return noalloc_fail(MERBIT_ECUDA, cudaGetErrorString(e));
+  return MERBIT_OK;
+}
+
+merbit_status merbit_spmv_noalloc_status(void* stream) {
+  set_last_error("");
+  void* base = nullptr;
+  if (cudaError_t e = scratch_address(&base); e != cudaSuccess)
+    return noalloc_fail(MERBIT_ECUDA, cudaGetErrorString(e));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* err = &static_cast<RedState*>(base)->err;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && h) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess && h) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return noalloc_fail(MERBIT_ECUDA, cudaGetErrorString(e));
+  if (h) {
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "a merbit_spmv_noalloc kernel gave up on a bounded wait (error bits 0x%x); "
+                  "the y of that call is incomplete",
+                  h);
+    return noalloc_fail(MERBIT_EDEVICE, msg);
+  }
   return MERBIT_OK;
 }
 

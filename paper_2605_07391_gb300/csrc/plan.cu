@@ -1,7 +1,8 @@
 // Plan construction (Sec. 4.1.2, Algorithm generate_tile) and the block
 // boundary data used by the SpMV commit.
-#include <mutex>
 #include <map>
+#include <mutex>
+#include <tuple>
 
 #include "merbit_internal.cuh"
 
@@ -166,19 +167,24 @@ cudaError_t build_dangling(merbit_plan_s* p, cudaStream_t st, unsigned long long
 }
 
 int persistent_grid(const void* kernel, int threads, size_t smem, size_t smem_max, int num_sms) {
+  // cudaFuncSetAttribute and the occupancy answer hold per device, so both
+  // caches are keyed by the current device as well as the kernel
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   static std::mutex mu;
-  static std::map<const void*, size_t> attr;                     // dynamic smem limit set per kernel
-  static std::map<std::pair<const void*, size_t>, int> cache;    // resident CTAs per SM
+  static std::map<std::pair<int, const void*>, size_t> attr;   // dynamic smem limit set
+  static std::map<std::tuple<int, const void*, size_t>, int> cache;   // resident CTAs per SM
   std::lock_guard<std::mutex> lock(mu);
-  auto key = std::make_pair(kernel, smem);
+  const auto key = std::make_tuple(dev, kernel, smem);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second * num_sms;
   // the limit is raised once to the largest size any plan of this kernel needs, never lowered
-  if (smem_max > 48 * 1024 && attr[kernel] < smem_max) {
+  size_t& lim = attr[std::make_pair(dev, kernel)];
+  if (smem_max > 48 * 1024 && lim < smem_max) {
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) !=
         cudaSuccess)
       return 0;
-    attr[kernel] = smem_max;
+    lim = smem_max;
   }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)

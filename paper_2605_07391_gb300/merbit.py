@@ -30,6 +30,7 @@ EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_
            "merbit_spmv_ex", "merbit_spmm",
            "merbit_ppr", "merbit_spmv_host", "merbit_spmv_host_async",
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
+           "merbit_spmv_noalloc_status",
            "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
            "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
            "merbit_batch_get_plan", "merbit_batch_destroy", "merbit_autotune_sigma", "merbit_bicgstab",
@@ -101,6 +102,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_batch_pagerank": [vp, i32, vp, dbl, dbl, i32, vp, vp, vp, ctypes.POINTER(i32), vp],
             "merbit_autotune_sigma": [vp, vp, i64, i64, i64, i32, vp, vp, i32, i32, vp,
                                       ctypes.POINTER(i32), vp],
+            "merbit_spmv_noalloc": [vp, vp, vp, vp, vp, i64, i64, i64, vp],
+            "merbit_spmv_noalloc_status": [vp],
             "merbit_bicgstab": [vp, vp, vp, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl),
                                 vp, ctypes.POINTER(i32), vp],
         }

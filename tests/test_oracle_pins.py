@@ -127,6 +127,42 @@ def _check_against_walk(row_ptr, sigma, omega=32):
     assert len(t["tile_x"]) == t["tile_num"] + 1 and len(t["lane_desc"]) == t["lane_num"]
 
 
+def _walk_block_rows(row_ptr, sigma, omega, W):
+    """Row of the merge-path coordinate at the start of every block of W tiles, plus the
+    end row n, from the literal walk: block b starts at step b*W*omega*sigma (Sec. 4.2's
+    y_bs; the last block's end y_be is the path's end, row n)."""
+    row_ptr = [int(v) for v in row_ptr]
+    n, m = len(row_ptr) - 1, row_ptr[-1]
+    total = m + n
+    rows_at, x, y = [0], 0, 0
+    for _ in range(total):
+        if x < row_ptr[y + 1]:
+            x += 1
+        else:
+            y += 1
+        rows_at.append(y)
+    per_block = W * omega * sigma
+    nb = -(-total // per_block)
+    return [rows_at[min(b * per_block, total)] for b in range(nb + 1)]
+
+
+@pytest.mark.parametrize("W", [8, 4, 16, 3])
+@pytest.mark.parametrize("sigma", [14, 7, 2])
+@pytest.mark.parametrize("case", range(5))
+def test_block_boundary_rows_match_walk(case, sigma, W):
+    if case < 3:
+        a = inputs.random_sparse(900 + 211 * case, 400, 0.02 * (case + 1), 40 + case,
+                                 empty_frac=0.25)
+        row_ptr = a.row_ptr
+    elif case == 3:
+        row_ptr = np.asarray(CASES[5][1], np.int64)           # rows of one tile each
+    else:
+        row_ptr = np.asarray([0] + [0] * 30 + [5000] * 3 + list(range(5001, 5101)), np.int64)
+    t = oracle.build_tile(row_ptr, sigma)
+    got = oracle.block_boundary_rows(t["tile_y"], t["tile_num"], W)
+    assert got.tolist() == _walk_block_rows(row_ptr, sigma, 32, W)
+
+
 def test_build_tile_invariants_rmat14():
     a = inputs.rmat_transition(14, 16, 1)
     sigma = 14
