@@ -179,27 +179,29 @@ struct EpiPageRank {
   static constexpr bool kReduce = true;
   PRParams p;
   const T* xold;
-  T a, c;
   double cd;
   __device__ __forceinline__ void init() {
     const double D = *p.d_in;
     cd = (p.alpha * D + 1.0 - p.alpha) * p.inv_n;
-    a = static_cast<T>(p.alpha);
-    c = static_cast<T>(cd);
   }
   __device__ __forceinline__ bool skip(const RedState* red) const {
     return *reinterpret_cast<const volatile int*>(&red->done) != 0;
   }
-  __device__ __forceinline__ void put(int r, T v, double& p0, double& p1) const {
+  // The step is measured on the update before it is rounded to T: once an FP32 iterate
+  // stops changing (each entry rounds back to itself), the rounded step reads 0 although
+  // the iterate is still about one rounding away from the fixed point, and a tolerance
+  // below that floor must not be reported as reached.
+  __device__ __forceinline__ void put(int r, double vd, double& p0, double& p1) const {
+    const T v = static_cast<T>(vd);
     static_cast<T*>(p.out)[r] = v;
-    p0 += fabs(static_cast<double>(v) - static_cast<double>(xold[r]));
+    p0 += fabs(vd - static_cast<double>(xold[r]));
     if (is_dangling(p.dang, r)) p1 += static_cast<double>(v);
   }
   __device__ __forceinline__ void row(int r, T s, double& p0, double& p1) const {
-    put(r, a * s + c, p0, p1);
+    put(r, fma(p.alpha, static_cast<double>(s), cd), p0, p1);
   }
   __device__ __forceinline__ void row64(int r, double s, double& p0, double& p1) const {
-    put(r, static_cast<T>(p.alpha * s + cd), p0, p1);
+    put(r, fma(p.alpha, s, cd), p0, p1);
   }
   __device__ __forceinline__ void finish(double A, double B, RedState* red) const {
     p.s_out[0] = A;

@@ -95,10 +95,14 @@ def test_mixed_precision_rmat14(cuda_device, mode):
 
 def test_plain_fp32_floor(cuda_device):
     """All-FP32 power iteration cannot reach an L1 residual of 1e-10: its iterates may stop
-    changing in FP32 (the step size it measures can reach 0), but the FP64 residual of its
-    answer, computed by the oracle with the master values, stays at the FP32 rounding floor."""
+    changing in FP32, but each update, measured before it is rounded to FP32, stays about
+    one rounding (u ||pi||_1, u = 2^-24) from the iterate, so the solver must report that it
+    did not converge; the FP64 residual of its answer, computed by the oracle with the
+    master values, stays at the FP32 rounding floor too (Sec. 5.5.1 iteration)."""
     a = inputs.rmat_transition(14, 16, 1)
     pi, info = _pr(a, torch.float32, tol=1e-10, max_iter=300)
+    assert not info["converged"] and info["iters"] == 300
+    assert 1e-9 < info["resid"] < 1e-6, info["resid"]
     r = oracle.pagerank_residual(a.row_ptr, a.col, a.val, pi, ALPHA)
     assert 1e-9 < r < 1e-5, r
 
