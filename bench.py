@@ -188,6 +188,68 @@ def oracle_timed(fn, unit_count: float, unit: str, sample: str, budget_s: float 
     return {"value": done / t_used, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample}
 
 
+# ---- the oracle on all host cores: worker processes (spawned, never forked after CUDA is
+# initialised) attach to the matrix in shared memory and multiply contiguous row blocks
+
+_SHARED = {}
+
+
+def _attach(spec):
+    from multiprocessing import shared_memory
+    for name, (shm_name, dtype, shape) in spec.items():
+        shm = shared_memory.SharedMemory(name=shm_name)
+        _SHARED[name] = (shm, np.ndarray(shape, dtype=dtype, buffer=shm.buf))
+
+
+def _oracle_block(bounds):
+    import oracle
+    r0, r1 = bounds
+    rp = _SHARED["row_ptr"][1]
+    lo, hi = int(rp[r0]), int(rp[r1])
+    oracle.spmv((rp[r0:r1 + 1] - lo).astype(np.int64), _SHARED["col"][1][lo:hi], _SHARED["val"][1][lo:hi],
+                _SHARED["x"][1])
+    return hi - lo
+
+
+def oracle_all_cores(a, x64: np.ndarray, budget_s: float, block_nnz: int = 4_000_000) -> dict:
+    """Float64 oracle SpMV on every host core: one spawned worker process per core, each
+    multiplying contiguous row blocks of about block_nnz nonzeros of the shared matrix;
+    blocks are handed out until budget_s of wall time is spent."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    cores = os.cpu_count() or 1
+    arrays = {"row_ptr": a.row_ptr, "col": a.col, "val": a.val, "x": x64}
+    shms, spec = [], {}
+    try:
+        for name, arr in arrays.items():
+            shm = shared_memory.SharedMemory(create=True, size=max(1, arr.nbytes))
+            np.ndarray(arr.shape, dtype=arr.dtype, buffer=shm.buf)[...] = arr
+            shms.append(shm)
+            spec[name] = (shm.name, arr.dtype.str, arr.shape)
+        bounds, r0 = [], 0
+        while r0 < a.n_rows:
+            r1 = int(np.searchsorted(a.row_ptr, a.row_ptr[r0] + block_nnz, side="right")) - 1
+            r1 = min(a.n_rows, max(r0 + 1, r1))
+            bounds.append((r0, r1))
+            r0 = r1
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores, initializer=_attach, initargs=(spec,)) as pool:
+            pool.map(_oracle_block, bounds[:cores])          # warm the workers
+            done, t0, i = 0, time.perf_counter(), 0
+            while time.perf_counter() - t0 < budget_s:
+                batch = [bounds[(i + j) % len(bounds)] for j in range(cores)]
+                done += sum(pool.map(_oracle_block, batch))
+                i += cores
+            wall = time.perf_counter() - t0
+        return {"value": done / wall / 1e9, "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
+                "sample": f"float64 oracle SpMV, {cores} spawned processes on row blocks of about "
+                          f"{block_nnz} nnz, {done} nnz in {wall:.1f} s wall"}
+    finally:
+        for shm in shms:
+            shm.close()
+            shm.unlink()
+
+
 def run_reference(args, rank, world):
     """Reference arm: the float64 CPU oracle on bounded samples of the same workload."""
     if rank != 0:
@@ -237,6 +299,121 @@ def algorithmic_bytes_f32(a, tiles) -> tuple[int, dict]:
     parts = {"vals_col": 8 * a.nnz, "x": 4 * a.n_cols, "y": 4 * a.n_rows,
              "lane_desc": 4 * max(0, lanes_in_normal), "tile_xy": 8 * (tile_num + 1)}
     return sum(parts.values()), {"r_f": float(marked.mean()) if marked.size else 0.0, **parts}
+
+
+def default_plan(rp, col, args, stream, sigma: int | None = None):
+    """The bench's plan: merbit_plan at the given sigma, then (with --hot H > 0) the plan's
+    hot-column table of up to H columns, kept if they hold --hot-min-cover of the
+    nonzeros.  The Plan gets hot_n and hot_cover attributes."""
+    import paper_2605_07391_gb300 as mb
+    p = mb.plan(rp, col, sigma=sigma or args.sigma, stream=stream)
+    p.hot_n, p.hot_cover = p.set_hot_columns(args.hot, args.hot_min_cover, stream=stream) if args.hot > 0 else (0, 0.0)
+    return p
+
+
+def algorithmic_bytes(a, tiles, val_bytes: int, vec_bytes: int) -> int:
+    """Algorithmic DRAM bytes of one product with the given value and vector widths: the
+    FP32 model of algorithmic_bytes_f32 with vals at val_bytes and x, y at vec_bytes."""
+    _, parts = algorithmic_bytes_f32(a, tiles)
+    return (val_bytes + 4) * a.nnz + vec_bytes * (a.n_cols + a.n_rows) + parts["lane_desc"] + parts["tile_xy"]
+
+
+def time_calls(fn, reps: int, stream) -> float:
+    """Mean ms per call of fn over reps calls (CUDA events on `stream`, after 5 warm-ups)."""
+    import torch
+    for _ in range(5):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_config1(args, dev, stream) -> dict:
+    """Configuration 1 (the small case): R-MAT scale 14 transition matrix, one SpMV in FP32
+    and FP64 (mean of 1000 calls) and the 100-update PageRank (alpha 0.85) in FP32 and FP64,
+    with the oracle's own times for the same work and the paper's ERR (relative l_inf error
+    against pi* = 210 oracle power updates, Sec. 5.5.1) of each 100-update result."""
+    import torch
+
+    import inputs
+    import oracle
+    import paper_2605_07391_gb300 as mb
+    scale, ef, seed = WORKLOADS["rmat14_transition"]
+    a = inputs.rmat_transition(scale, ef, seed)
+    x64 = inputs.uniform_vector(a.n_cols, 2)
+    rp, col = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col).to(dev)
+    p = mb.plan(rp, col, stream=stream)
+    tiles = p.tiles()
+    hbm = peaks()[0]
+    star = oracle.pagerank(a.row_ptr, a.col, a.val, 0.85, tol=0.0, fixed_iters=210)["pi"]
+    res = {"workload": "rmat14_transition", "n": a.n_rows, "nnz": a.nnz}
+    for name, dt, vb in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        vals = torch.from_numpy(a.val).to(dev, dt)
+        x = torch.from_numpy(x64).to(dev, dt)
+        y = torch.empty(a.n_rows, dtype=dt, device=dev)
+        ms = time_calls(lambda: mb.spmv(p, vals, x, y, stream=stream), 1000, stream)
+        alg = algorithmic_bytes(a, tiles, vb, vb)
+        mb.pagerank(p, vals, 0.85, tol=0.0, max_iter=100, stream=stream)          # warm
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        pi, info = mb.pagerank(p, vals, 0.85, tol=0.0, max_iter=100, stream=stream)
+        torch.cuda.synchronize(dev)
+        pr_ms = (time.perf_counter() - t0) * 1e3
+        res[name] = {"spmv_ms": ms, "gnnz_s": a.nnz / (ms * 1e-3) / 1e9, "roofline_frac": alg / (ms * 1e-3) / 1e9 / hbm,
+                     "pagerank_100_ms": pr_ms,
+                     "pagerank_err_vs_pi_star": oracle.relative_linf_error(pi.double().cpu().numpy(), star)}
+    t0 = time.perf_counter()
+    oracle.spmv(a.row_ptr, a.col, a.val, x64)
+    res["oracle_spmv_ms"] = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    oracle.pagerank(a.row_ptr, a.col, a.val, 0.85, tol=0.0, fixed_iters=100)
+    res["oracle_pagerank_100_ms"] = (time.perf_counter() - t0) * 1e3
+    res["oracle_cores"] = 1
+    p.destroy()
+    return res
+
+
+def run_config2(args, dev, stream) -> dict:
+    """Configuration 2 (irregular-structure stress, the degree question of Sec. 5.2.2):
+    the R-MAT scale 22 matrix with values U(0,1] as is (a), with 30 % of its rows emptied
+    (b), with 16 hub rows of 1M-4M nonzeros (c), and the Erdos-Renyi 2^22 matrix with 16
+    nonzeros per row (d); FP32 and FP64 SpMV, each the mean of --config2-calls calls with the
+    plan reused (plan built as the bench's default plan)."""
+    import torch
+
+    import inputs
+    import paper_2605_07391_gb300 as mb
+    hbm = peaks()[0]
+    base = inputs.rmat_uniform(22, 16, 3, 3)
+    makers = {"a_rmat22": lambda: base, "b_empty30": lambda: inputs.empty_rows(base, 0.3, 4),
+              "c_hubs16": lambda: inputs.add_hubs(base, 16, 1_000_000, 4_000_000, 5),
+              "d_er22": lambda: inputs.erdos_renyi(1 << 22, 16, 6)}
+    x64 = inputs.uniform_vector(1 << 22, 2)
+    res = {"calls": args.config2_calls}
+    for name, make in makers.items():
+        a = make()
+        rp, col = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col).to(dev)
+        p = default_plan(rp, col, args, stream)
+        tiles = p.tiles()
+        rec = {"nnz": a.nnz, "hot_columns": p.hot_n}
+        for dname, dt, vb in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+            vals = torch.from_numpy(a.val).to(dev, dt)
+            x = torch.from_numpy(x64[:a.n_cols]).to(dev, dt)
+            y = torch.empty(a.n_rows, dtype=dt, device=dev)
+            ms = time_calls(lambda: mb.spmv(p, vals, x, y, stream=stream), args.config2_calls, stream)
+            alg = algorithmic_bytes(a, tiles, vb, vb)
+            rec[dname] = {"ms": ms, "gnnz_s": a.nnz / (ms * 1e-3) / 1e9,
+                          "roofline_frac": alg / (ms * 1e-3) / 1e9 / hbm}
+            del vals, x, y
+        p.sync(stream)
+        p.destroy()
+        res[name] = rec
+        del a, rp, col
+    return res
 
 
 def run_batched(args, dev, stream) -> dict:
@@ -510,6 +687,40 @@ def run_autograd(args, dev, stream) -> dict:
     return res
 
 
+def summarize(out: dict) -> dict:
+    """The headline figures in a few hundred bytes, the last key of the line."""
+    def r(v, d=4):
+        return None if v is None else round(float(v), d)
+    rf = out["roofline"]
+    sm = {"spmv_f32_ms": r(rf["mean_launch_ms"]), "gnnz_s": r(out["value"], 1), "frac": r(rf["frac"]),
+          "plan_ms": r(out["plan_ms"], 2), "hot_cols": out["hot_table"]["columns"],
+          "hot_cover": r(out["hot_table"]["cover"], 3)}
+    if "gather_floor" in out:
+        g = out["gather_floor"]
+        sm.update({"floor_ms": r(g["ms"]), "no_hot_ms": r(g["without_hot_table"]["spmv_ms"]),
+                   "no_hot_floor_ms": r(g["without_hot_table"]["floor_ms"])})
+    if "spmv_other" in out:
+        o = out["spmv_other"]
+        sm.update({"f64_ms": r(o["f64"]["ms"]), "f64_sigma": o["f64"]["sigma"], "bf16_ms": r(o["bf16_vals"]["ms"])})
+    if "pagerank" in out:
+        pr = out["pagerank"]
+        sm["pagerank"] = {k: [r(v["ms"], 1), v["converged"], v.get("oracle_l1_residual") and float(f"{v['oracle_l1_residual']:.2e}"),
+                              float(f"{v['err_vs_pi_star']:.2e}")]
+                          for k, v in pr.items() if isinstance(v, dict)}
+        sm["mixed_vs_ir_f32"] = r(pr.get("mixed_vs_ir_f32_speedup"), 3)
+    if "config2" in out:
+        sm["config2_gnnz_f32_f64"] = {k: [r(v["f32"]["gnnz_s"], 1), r(v["f64"]["gnnz_s"], 1)]
+                                      for k, v in out["config2"].items() if isinstance(v, dict)}
+    if "config1" in out:
+        c = out["config1"]
+        sm["config1_ms"] = {"spmv_f32": r(c["f32"]["spmv_ms"]), "pr100_f32": r(c["f32"]["pagerank_100_ms"], 2),
+                            "pr100_f64": r(c["f64"]["pagerank_100_ms"], 2), "oracle_pr100": r(c["oracle_pagerank_100_ms"], 1)}
+    if "cpu_all_cores" in out:
+        sm["oracle_gnnz_1core_allcores"] = [r(out["cpu_baseline"]["value"]), r(out["cpu_all_cores"]["value"]),
+                                            out["cpu_all_cores"]["cores"]]
+    return sm
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -536,6 +747,14 @@ def main():
     ap.add_argument("--inner-sweeps", type=int, default=0,
                     help="max inner sweeps per refinement step (0: the tuned setting of each mode)")
     ap.add_argument("--sigma", type=int, default=14, help="steps per lane of the plan")
+    ap.add_argument("--hot", type=int, default=8192,
+                    help="hot-column table of the plans: up to this many columns (0: none)")
+    ap.add_argument("--hot-min-cover", type=float, default=0.05,
+                    help="keep a --hot table only if its columns hold this fraction of the nonzeros")
+    ap.add_argument("--no-config1", action="store_true", help="skip the R-MAT scale 14 runs")
+    ap.add_argument("--no-config2", action="store_true", help="skip the R-MAT scale 22 stress runs")
+    ap.add_argument("--config2-calls", type=int, default=1000, help="SpMV calls per stress matrix")
+    ap.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle leg")
     args = ap.parse_args()
     rank, world, local = dist_setup()
     if args.impl == "reference":
@@ -576,6 +795,11 @@ def main():
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     plan_ms = ev0.elapsed_time(ev1)
+    # the hot-column table (one-time, like the plan), timed on its own
+    t0 = time.perf_counter()
+    p.hot_n, p.hot_cover = p.set_hot_columns(args.hot, args.hot_min_cover, stream=stream) if args.hot > 0 else (0, 0.0)
+    torch.cuda.synchronize(dev)
+    hot_ms = (time.perf_counter() - t0) * 1e3
     tiles = p.tiles()
     alg_bytes, alg_parts = algorithmic_bytes_f32(a, tiles)
 
@@ -635,10 +859,29 @@ def main():
                         "mean_launch_ms": mean_launch_ms,
                         "median_launch_ms": statistics.median(launch_ms)},
            "plan_ms": plan_ms, "gen_s": gen_s,
+           "hot_table": {"max_columns": args.hot, "columns": p.hot_n, "cover": p.hot_cover,
+                         "build_ms": hot_ms},
            # each step launches the SpMV kernel and its boundary-row finalize kernel
            "gpu_launches": 2 * K, "clocks": clock_info}
 
     if rank == 0:
+        # ---- the floor of the gathers: the product's x gather alone at the split kernel's
+        # shared-memory footprint (merbit_gather_probe), and both without the hot table
+        sink = torch.zeros(4096, device=dev)
+        floor_ms = time_calls(lambda: p.gather_probe(x, sink, stream=stream), 50, stream)
+        q = mb.plan(row_ptr, col, sigma=args.sigma, stream=stream)
+        plain_ms = time_calls(lambda: mb.spmv(q, v32, x, y, stream=stream), 50, stream)
+        plain_floor_ms = time_calls(lambda: q.gather_probe(x, sink, stream=stream), 50, stream)
+        q.destroy()
+        out["gather_floor"] = {
+            "ms": floor_ms, "spmv_over_floor": mean_launch_ms / floor_ms,
+            "frac_at_floor": alg_bytes / (floor_ms * 1e-3) / 1e9 / hbm_peak,
+            "without_hot_table": {"spmv_ms": plain_ms, "floor_ms": plain_floor_ms,
+                                  "frac": alg_bytes / (plain_ms * 1e-3) / 1e9 / hbm_peak},
+            "probe": "merbit_gather_probe: the x[col[k]] loads of every nonzero (hot-table slots from "
+                     "shared memory), column stream read coalesced, split kernel's grid and shared memory"}
+        mb.spmv(p, v32, x, y, stream=stream)
+
         # ---- end to end through the host-buffer entry point (pinned buffers)
         xh = x.cpu().pin_memory()
         yh = torch.empty(a.n_rows, dtype=torch.float32).pin_memory()
@@ -675,7 +918,7 @@ def main():
         s64, t64 = mb.autotune_sigma(row_ptr, col, v64, candidates=(14, 12, 10, 8, 7), reps=3,
                                      stream=stream)
         ev0.record(stream)
-        p64 = p if s64 == p.sigma else mb.plan(row_ptr, col, sigma=s64, stream=stream)
+        p64 = p if s64 == p.sigma else default_plan(row_ptr, col, args, stream, sigma=s64)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         plan64_ms = plan_ms if p64 is p else ev0.elapsed_time(ev1)
@@ -692,7 +935,8 @@ def main():
             torch.cuda.synchronize(dev)
             ms = e0.elapsed_time(e1) / 100
             other[name] = {"gnnz_s": a.nnz / (ms * 1e-3) / 1e9, "ms": ms}
-        other["f64"].update({"sigma": s64, "autotune_ms_per_spmv": t64, "plan_ms": plan64_ms})
+        other["f64"].update({"sigma": s64, "autotune_ms_per_spmv": t64, "plan_ms": plan64_ms,
+                             "hot_columns": p64.hot_n})
         out["spmv_other"] = other
         del lo, y64, x64d
 
@@ -700,6 +944,12 @@ def main():
         if not args.no_pagerank:
             import oracle
             pr = {}
+            # pi* of the paper's ERR (Sec. 5.5.1): 210 updates of the FP64 power method (here on
+            # the device), with the oracle's FP64 residual of it beside it
+            star, _ = mb.pagerank(p64, v64, 0.85, tol=0.0, max_iter=210, stream=stream)
+            star = star.cpu().numpy()
+            if not args.no_oracle_check:
+                pr["pi_star_oracle_l1_residual"] = oracle.pagerank_residual(a.row_ptr, a.col, a.val, star, 0.85)
             runs = [("ir_bf16", torch.float64), ("ir_f16", torch.float64), ("ir_f32", torch.float64),
                     ("plain_f64", torch.float64), ("plain_f32", torch.float32)]
             # refinement settings (inner stop eta, sweep cap) tuned per mode on this workload:
@@ -711,7 +961,8 @@ def main():
                 eta, cap = tuned.get(mode, (0.0, 32))
                 if args.inner_sweeps:
                     eta, cap = 0.0, args.inner_sweeps
-                kw = dict(tol=1e-10, max_iter=400 if mode == "plain" else 60, mode=mode,
+                kw = dict(tol=1e-10, max_iter=(150 if dt == torch.float32 else 400) if mode == "plain" else 60,
+                          mode=mode,
                           inner_sweeps=cap, inner_tol=eta, stream=stream)
                 pp, pp_plan_ms = (p64, plan64_ms) if name == "plain_f64" else (p, plan_ms)
                 mb.pagerank(pp, vals, 0.85, **dict(kw, max_iter=2, tol=0.0))   # warm
@@ -726,8 +977,9 @@ def main():
                 if mode != "plain":
                     rec["inner_sweeps_cap"] = cap
                     rec["inner_eta"] = eta
+                pin = pi.double().cpu().numpy()
+                rec["err_vs_pi_star"] = oracle.relative_linf_error(pin, star)
                 if not args.no_oracle_check:
-                    pin = pi.double().cpu().numpy()
                     r = oracle.pagerank_residual(a.row_ptr, a.col, a.val, pin, 0.85)
                     rec["oracle_l1_residual"] = r
                     rec["l1_err_bound_vs_fp64_fixed_point"] = r / 0.15
@@ -738,6 +990,12 @@ def main():
                 out["pagerank"]["mixed_vs_ir_f32_speedup"] = pr["ir_f32"]["ms"] / pr["ir_bf16"]["ms"]
             if pr["plain_f64"]["converged"]:
                 out["pagerank"]["mixed_vs_plain_f64_speedup"] = pr["plain_f64"]["ms"] / pr["ir_bf16"]["ms"]
+
+        # ---- configuration 1 (R-MAT scale 14) and configuration 2 (R-MAT scale 22 stress)
+        if not args.no_config1:
+            out["config1"] = run_config1(args, dev, stream)
+        if not args.no_config2:
+            out["config2"] = run_config2(args, dev, stream)
 
         # ---- batching: SpMM and personalised PageRank on R-MAT scale 22, k = 8 and 32
         if not args.no_batched:
@@ -761,6 +1019,10 @@ def main():
                                "kind": "oracle",
                                "sample": f"float64 oracle SpMV on contiguous row blocks of ~1/64 of "
                                          f"the matrix, {nnz_done} nnz in {t_used:.1f} s"}
+        out["host"] = {"nproc": os.cpu_count(), "machine": os.uname().machine}
+        if not args.no_all_cores:
+            out["cpu_all_cores"] = oracle_all_cores(a, x64, args.cpu_budget)
+        out["summary"] = summarize(out)
         print(json.dumps(out), flush=True)
         if p64 is not p:
             p64.destroy()

@@ -132,6 +132,47 @@ enum {
  * takes effect at the next launch).  Errors: EINVAL (NULL plan, unknown kernel). */
 merbit_status merbit_plan_set_kernel(merbit_plan_t plan, int kernel);
 
+/*
+ * merbit_plan_set_hot_columns — (re)build the plan's hot-column table, or drop it
+ * (max_hot = 0).  No counterpart in the paper: it serves the x gather of the SpMV
+ * (Sec. 4.2) on GB300.  The columns referenced by the most nonzeros (at most max_hot,
+ * each used at least twice) are sorted by use; the plan keeps a copy of col_idx in
+ * which each of them is replaced by its table slot, and every product launch copies x
+ * at those columns into the shared memory of each CTA once and takes the gathers of
+ * those nonzeros from there.  A launch uses the table only when all of it fits beside
+ * its block kernel's stages without lowering the resident CTAs per SM (otherwise it
+ * streams col_idx as before); results agree with the plain gather bit for bit in the
+ * products, to rounding in the sums.  The table is kept only if its columns hold at
+ * least min_cover (in [0, 1]) of the nonzeros.  Costs 4 bytes per nonzero of device
+ * memory and a few passes over col_idx; synchronises `stream`.  *hot_n_out and
+ * *cover_out (host, may be NULL) receive the number of table columns (0: none) and the
+ * fraction of the nonzeros they hold.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+merbit_status merbit_plan_set_hot_columns(merbit_plan_t plan, int max_hot, double min_cover,
+                                          void* stream, int* hot_n_out, double* cover_out);
+
+/*
+ * merbit_gather_probe — a measurement aid with no counterpart in the paper: one pass of
+ * the SpMV's x gather alone (the x[col[k]] of Sec. 4.2's products) over the plan's
+ * nonzeros, with the grid, block size and dynamic shared memory of the plan's
+ * split-kernel product launch for x of type xdt (F32 or F64), the hot-column table
+ * included when that launch would use it.  The column stream is read coalesced; every
+ * gathered value is summed and each CTA writes its sum to sink (device, at least 4096
+ * entries of xdt).  Timing it beside the product gives the cost of the gathers at the
+ * kernel's shared-memory footprint.  Asynchronous on `stream`.  Errors: EINVAL, ECUDA.
+ */
+merbit_status merbit_gather_probe(merbit_plan_t plan, merbit_dtype xdt, const void* x, void* sink,
+                                  void* stream);
+
+/* Test aid (no counterpart in the paper): the number of polls after which a stage wait
+ * of the plan's SpMV block kernels gives up (polls < 0 restores the default, 2^22).  A
+ * wait that gives up sets the plan's error bit; the kernel then waits, with the default
+ * limit, for its own copies in flight and returns, and merbit_plan_sync (or the next
+ * solver call) reports MERBIT_EDEVICE and clears the state.  polls = 0 makes every
+ * launch give up at its first stage wait, which exercises that path without any fault.
+ * Errors: EINVAL (NULL plan). */
+merbit_status merbit_plan_set_wait_limit(merbit_plan_t plan, int polls);
+
 /* Synchronise `stream` and report a kernel-side error of this plan's earlier
  * asynchronous calls (EDEVICE; the plan's device state is reset). */
 merbit_status merbit_plan_sync(merbit_plan_t plan, void* stream);

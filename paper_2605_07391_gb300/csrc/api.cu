@@ -14,6 +14,7 @@ cudaError_t host_async_wait(const merbit_plan_s* p);
 void host_async_release(const merbit_plan_s* p);
 cudaError_t build_tiles(const merbit_plan_s* p, const int32_t* row_ptr, cudaStream_t st);
 cudaError_t build_dangling(merbit_plan_s* p, cudaStream_t st, unsigned long long* host_count);
+void free_hot_table(merbit_plan_s* p);
 }  // namespace merbit
 
 using namespace merbit;
@@ -58,6 +59,7 @@ size_t dtype_size(merbit_dtype d) {
 void free_plan(merbit_plan_s* p) {
   if (!p) return;
   host_async_release(p);
+  free_hot_table(p);
   cudaFree(p->tile_x);
   cudaFree(p->tile_y);
   cudaFree(p->lane_desc);
@@ -418,6 +420,12 @@ merbit_status merbit_plan_set_kernel(merbit_plan_t p, int kernel) {
   if (kernel < MERBIT_KERNEL_AUTO || kernel > MERBIT_KERNEL_SPLIT)
     return fail(MERBIT_EINVAL, "kernel must be MERBIT_KERNEL_AUTO, _CLASSIC or _SPLIT");
   p->spmv_kernel = kernel;
+  return MERBIT_OK;
+}
+
+merbit_status merbit_plan_set_wait_limit(merbit_plan_t p, int polls) {
+  if (merbit_status s = check_plan(p)) return s;
+  p->wait_limit = polls < 0 ? kSpinLimit : (uint32_t)polls;
   return MERBIT_OK;
 }
 

@@ -36,6 +36,10 @@ struct Geometry {
   const uint32_t* tile_y;
   const uint32_t* lane_desc;
   const int32_t* col;
+  const int32_t* col_stage;   // column stream of the SpMV stages: col, or its hot-tagged copy
+  const int32_t* hot_list;    // column of each hot-table slot
+  int hot_n;                  // hot columns cached in shared memory by this launch (0: none)
+  uint32_t wait_limit;        // polls of a stage wait before it gives up (drains use kSpinLimit)
   const int32_t* bnd_row;
   const int32_t* bnd_slot;
   double* bnd_acc;
@@ -58,8 +62,15 @@ struct merbit_plan_s {
   int64_t n_rows = 0, n_cols = 0, nnz = 0;
   int sigma = 14, tiles_per_block = merbit::kTilesPerBlock;
   int spmv_kernel = 0;                   // MERBIT_KERNEL_AUTO / _CLASSIC / _SPLIT
+  uint32_t wait_limit = merbit::kSpinLimit;   // polls of a stage wait (test hook lowers it)
   int64_t tile_num = 0, lane_num = 0, nb = 0;
   const int32_t* col = nullptr;          // borrowed
+  // hot-column table: col_hot is a copy of col in which a column held in the table is
+  // replaced by ~slot; hot_list[slot] is that column (slots by decreasing use)
+  int32_t* col_hot = nullptr;
+  int32_t* hot_list = nullptr;
+  int hot_n = 0;
+  double hot_cover = 0.0;                // fraction of the nonzeros in hot columns
   uint32_t* tile_x = nullptr;
   uint32_t* tile_y = nullptr;
   uint32_t* lane_desc = nullptr;
@@ -85,6 +96,8 @@ struct merbit_plan_s {
   merbit::Geometry geom() const {
     merbit::Geometry g;
     g.tile_x = tile_x; g.tile_y = tile_y; g.lane_desc = lane_desc; g.col = col;
+    g.col_stage = col; g.hot_list = hot_list; g.hot_n = 0;   // a launch opts in to the table
+    g.wait_limit = wait_limit;
     g.bnd_row = bnd_row; g.bnd_slot = bnd_slot;
     g.bnd_acc = bnd_acc; g.part = part; g.red = red;
     g.n_rows = (int)n_rows; g.nnz = (int)nnz; g.steps = (int)(nnz + n_rows);
@@ -166,8 +179,18 @@ cudaError_t ppr_update(const merbit_plan_s* p, const float* vals, const float* X
 // pi += delta (FP64) with delta = the refinement's latest inner iterate; s_out[1] = dangling mass
 cudaError_t ir_apply(const merbit_plan_s* p, double* pi, double* s_out, cudaStream_t st);
 
+// Launch configuration of the split kernel's plain product (f32 or f64 values and
+// vectors) for a plan: grid, dynamic shared memory, geometry (with the hot-column table
+// if that launch takes it); false if it cannot be launched.
+bool split_config_f32(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem);
+bool split_config_f64(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem);
+
 // Largest grid worth launching for a kernel (SMs x resident CTAs), cached.
 // smem_max: the largest dynamic shared memory any launch of this kernel may use.
 int persistent_grid(const void* kernel, int threads, size_t smem, size_t smem_max, int num_sms);
+
+// Dynamic shared memory one CTA of `kernel` may use while `per_sm` of its CTAs stay
+// resident on an SM of the current device (0 on error).
+size_t smem_room(const void* kernel, int per_sm);
 
 }  // namespace merbit

@@ -193,4 +193,30 @@ int persistent_grid(const void* kernel, int threads, size_t smem, size_t smem_ma
   return per_sm * num_sms;
 }
 
+size_t smem_room(const void* kernel, int per_sm) {
+  if (per_sm <= 0) return 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> stat;   // static smem per kernel
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(dev, kernel);
+  auto it = stat.find(key);
+  if (it == stat.end()) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 0;
+    it = stat.emplace(key, fa.sharedSizeBytes).first;
+  }
+  int per_sm_total = 0, reserved = 0, optin = 0;
+  if (cudaDeviceGetAttribute(&per_sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  const long long share = (long long)per_sm_total / per_sm - reserved - (long long)it->second;
+  const long long cap = (long long)optin - (long long)it->second;
+  const long long room = share < cap ? share : cap;
+  return room > 0 ? (size_t)room : 0;
+}
+
 }  // namespace merbit

@@ -17,4 +17,8 @@ cudaError_t spmv_pr_f32(const merbit_plan_s* p, const float* vals, const float* 
   return launch_spmv<float, float, float>(p, vals, x, epi, st);
 }
 
+bool split_config_f32(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem) {
+  return split_config<float, float, float, EpiPlain<float, float>>(p, g, grid, smem, true);
+}
+
 }  // namespace merbit

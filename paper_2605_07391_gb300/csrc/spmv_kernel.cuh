@@ -78,8 +78,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for an mbarrier phase with an iteration cap; false if the cap expired.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint32_t limit = kSpinLimit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -115,6 +116,23 @@ __device__ __forceinline__ double ld_x(const double* p, uint64_t pol) {
   double v;
   asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
   return v;
+}
+
+// The gather of x[c] when `pred` holds; v keeps its value otherwise (no access is made).
+__device__ __forceinline__ void ld_x_if(float& v, const float* p, bool pred, uint64_t pol) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+      "@q ld.global.nc.L2::cache_hint.f32 %0, [%1], %3;\n\t}"
+      : "+f"(v)
+      : "l"(p), "r"((uint32_t)pred), "l"(pol));
+}
+
+__device__ __forceinline__ void ld_x_if(double& v, const double* p, bool pred, uint64_t pol) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+      "@q ld.global.nc.L2::cache_hint.f64 %0, [%1], %3;\n\t}"
+      : "+d"(v)
+      : "l"(p), "r"((uint32_t)pred), "l"(pol));
 }
 
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t pol) {
@@ -377,7 +395,7 @@ struct Stages {
     const uint32_t bc = (uint32_t)(in.endc - in.a0c) * 4u;
     mbar_arrive_expect_tx(bar, bv + bc);
     if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, bar, pol);
-    if (bc) bulk_g2s(sc(s), g.col + in.a0c, bc, bar, pol);
+    if (bc) bulk_g2s(sc(s), g.col_stage + in.a0c, bc, bar, pol);
   }
 
   // The stage's product slots (over the values, or over the column indices for 16-bit
@@ -392,12 +410,18 @@ struct Stages {
     }
   }
 
-  // product k - pb of a staged nonzero k: val * x[col] (x[col] for UnitVal)
+  // x[col] of a staged nonzero k.  A staged column c < 0 names hot-table slot ~c, whose
+  // x value this CTA holds in shared memory (tab); the other columns are gathered from
+  // x in global memory.  Nonzeros past the staged range read the plain column array.
   template <typename XT>
-  __device__ __forceinline__ void gather(int s, const StageInfo& in, int k, const XT* x, uint64_t pol_x,
-                                         AT& xv) const {
+  __device__ __forceinline__ void gather(int s, const StageInfo& in, int k, const XT* x, const XT* tab,
+                                         uint64_t pol_x, AT& xv) const {
     const int c = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
-    xv = static_cast<AT>(ld_x(x + c, pol_x));
+    const bool hot = c < 0;
+    XT v = XT(0);
+    if (hot) v = tab[~c];
+    ld_x_if(v, x + c, !hot, pol_x);
+    xv = static_cast<AT>(v);
   }
   __device__ __forceinline__ AT product(int s, const StageInfo& in, int k, AT xv) const {
     if constexpr (IsUnit<VT>::value) {
@@ -407,6 +431,13 @@ struct Stages {
     }
   }
 };
+
+// This CTA's copy of the hot-column table: tab[i] = x[hot_list[i]] for i < g.hot_n,
+// loaded by all threads of the CTA at the start of a launch (the caller synchronises).
+template <typename XT>
+__device__ __forceinline__ void fill_hot(const Geometry& g, const XT* x, XT* tab, uint64_t pol_x) {
+  for (int i = threadIdx.x; i < g.hot_n; i += blockDim.x) tab[i] = ld_x(x + __ldg(g.hot_list + i), pol_x);
+}
 
 // The blocks a CTA walks: all blocks in order, or the epilogue's list (*block_count
 // entries, read at kernel start).
@@ -522,6 +553,11 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (blockIdx.x < nbl) st.issue(0, st.span(blk(blockIdx.x)), &info[0], &mbar[0]);
     if (blockIdx.x + G < nbl) st.issue(1, st.span(blk(blockIdx.x + G)), &info[1], &mbar[1]);
   }
+  XT* tab = reinterpret_cast<XT*>(dyn_smem + 2 * st.stb);
+  if (g.hot_n > 0) {
+    fill_hot(g, x, tab, pol_x);
+    __syncthreads();
+  }
 
   double p0 = 0.0, p1 = 0.0;
   int it = 0;
@@ -546,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     const bool refill = (tid == 0) && (kb + 2 * G < nbl);
     if (refill) next = st.span(blk(kb + 2 * G));
 
-    const bool ok = mbar_wait_bounded(&mbar[s], par);
+    const bool ok = mbar_wait_bounded(&mbar[s], par, g.wait_limit);
     if (__syncthreads_or(!ok)) {
       // expired wait: record it, let this CTA's copies land (bounded), leave
       if (tid == 0) atomicOr(&g.red->err, 1);
@@ -566,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       for (int u = 0; u < kSigmaMax; ++u) {
         const int e = tid + u * kThreads;
         xv[u] = AT(0);
-        if (e < cnt) st.gather(s, in, in.x_bs + e, x, pol_x, xv[u]);
+        if (e < cnt) st.gather(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
       }
 #pragma unroll
       for (int u = 0; u < kSigmaMax; ++u) {
@@ -689,6 +725,11 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
     for (; issued < S && issued < nmine; ++issued)
       st.issue(issued, st.span(blk(blockIdx.x + issued * G)), &info[issued], &full[issued]);
   }
+  XT* tab = reinterpret_cast<XT*>(dyn_smem + S * st.stb);
+  if (g.hot_n > 0) {
+    fill_hot(g, x, tab, pol_x);
+    __syncthreads();
+  }
 
   if (tid >= kSplitConsumers) {
     // ---- producers: products val * x[col] of each block (load_smem), then the zeroed
@@ -697,7 +738,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
     for (int i = 0; i < nmine; ++i) {
       const int s = i % S;
       // a warp gives up as a whole, so none of its lanes is left at the __syncwarp below
-      const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(i / S) & 1u);
+      const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(i / S) & 1u, g.wait_limit);
       if (__any_sync(0xffffffffu, !ok)) {
         if (lane == 0) {
           atomicOr(&g.red->err, 1);
@@ -718,7 +759,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
         for (int u = 0; u < NB; ++u) {
           const int e = base + pt + u * kSplitProducers;
           xv[u] = AT(0);
-          if (e < cnt) st.gather(s, in, in.x_bs + e, x, pol_x, xv[u]);
+          if (e < cnt) st.gather(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
         }
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
@@ -759,7 +800,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       const bool refill = (tid == 0) && (i + S < nmine);
       if (refill) next = st.span(blk(kb + S * G));
 
-      const bool ok = mbar_wait_bounded(&ready[s], (uint32_t)(i / S) & 1u);
+      const bool ok = mbar_wait_bounded(&ready[s], (uint32_t)(i / S) & 1u, g.wait_limit);
       if (consumers_or(!ok)) {
         if (tid == 0) {
           atomicOr(&g.red->err, 1);
@@ -887,6 +928,40 @@ __global__ void __launch_bounds__(256) merbit_finalize_kernel(const Geometry g, 
   }
 }
 
+// Launch geometry of one block kernel: the plan's hot-column table is added to the
+// stages' shared memory when the whole table fits without lowering the number of
+// resident CTAs per SM; otherwise the launch streams the plain column array.
+template <typename XT>
+inline size_t add_hot_table(const merbit_plan_s* p, Geometry& g, const void* kern, size_t stages,
+                            int per_sm) {
+  if (p->hot_n <= 0 || !p->col_hot || per_sm <= 0) return stages;
+  const size_t need = stages + ((sizeof(XT) * (size_t)p->hot_n + 15) & ~size_t(15));
+  if (need > smem_room(kern, per_sm)) return stages;
+  g.col_stage = p->col_hot;
+  g.hot_list = p->hot_list;
+  g.hot_n = p->hot_n;
+  return need;
+}
+
+// Grid, dynamic shared memory and geometry (with or without the hot-column table) of the
+// split kernel's launch for a plan; false if two of its CTAs do not fit on an SM (or
+// none does, when `forced`).
+template <typename VT, typename XT, typename AT, typename Epi>
+bool split_config(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem, bool forced) {
+  auto kern = merbit_spmv_split_kernel<VT, XT, AT, Epi>;
+  const void* kp = reinterpret_cast<const void*>(kern);
+  const size_t stages = kSplitStages * stage_bytes<VT>(p->sigma);
+  const size_t stages_max = kSplitStages * stage_bytes<VT>(kSigmaMax);
+  grid = persistent_grid(kp, kSplitThreads, stages, stages_max, p->num_sms);
+  if (grid <= 0 || (!forced && grid < 2 * p->num_sms)) return false;
+  smem = add_hot_table<XT>(p, g, kp, stages, grid / p->num_sms);
+  if (smem != stages) grid = persistent_grid(kp, kSplitThreads, smem, std::max(smem, stages_max), p->num_sms);
+  if (grid <= 0) return false;
+  if ((int64_t)grid > p->nb) grid = (int)p->nb;
+  if (grid > kMaxParts) grid = kMaxParts;
+  return true;
+}
+
 template <typename VT, typename XT, typename AT, typename Epi>
 cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, const Epi& epi,
                         cudaStream_t st) {
@@ -894,38 +969,36 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   // The split kernel is the default for 32- and 64-bit values while two of its CTAs fit
   // on an SM (measured on sm_103a, R-MAT scale 21 and 24: 15-30 % faster than the classic
   // kernel there, slower with one CTA per SM, level for 16-bit values).
+  Geometry g = p->geom();
   int grid = 0;
   bool split = false;
   if (p->spmv_kernel == MERBIT_KERNEL_SPLIT ||
       (p->spmv_kernel == MERBIT_KERNEL_AUTO && sizeof(VT) >= 4)) {
-    auto kern = merbit_spmv_split_kernel<VT, XT, AT, Epi>;
-    const size_t smem = kSplitStages * stage_bytes<VT>(p->sigma);
-    const size_t smem_max = kSplitStages * stage_bytes<VT>(kSigmaMax);
-    grid = persistent_grid(reinterpret_cast<const void*>(kern), kSplitThreads, smem, smem_max,
-                           p->num_sms);
-    if (grid <= 0 && p->spmv_kernel == MERBIT_KERNEL_SPLIT) return cudaErrorInvalidConfiguration;
-    split = grid > 0 && (p->spmv_kernel == MERBIT_KERNEL_SPLIT || grid >= 2 * p->num_sms);
-    if (split) {
-      if ((int64_t)grid > p->nb) grid = (int)p->nb;
-      if (grid > kMaxParts) grid = kMaxParts;
-      kern<<<grid, kSplitThreads, smem, st>>>(p->geom(), vals, x, epi);
-    }
+    size_t smem = 0;
+    const bool forced = p->spmv_kernel == MERBIT_KERNEL_SPLIT;
+    split = split_config<VT, XT, AT, Epi>(p, g, grid, smem, forced);
+    if (!split && forced) return cudaErrorInvalidConfiguration;
+    if (split) merbit_spmv_split_kernel<VT, XT, AT, Epi><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
   }
   if (!split) {
+    g = p->geom();
     auto kern = merbit_spmv_kernel<VT, XT, AT, Epi>;
-    const size_t smem = 2 * stage_bytes<VT>(p->sigma);
-    const size_t smem_max = 2 * stage_bytes<VT>(kSigmaMax);
-    grid = persistent_grid(reinterpret_cast<const void*>(kern), kThreads, smem, smem_max,
-                           p->num_sms);
+    const void* kp = reinterpret_cast<const void*>(kern);
+    const size_t stages = 2 * stage_bytes<VT>(p->sigma);
+    const size_t stages_max = 2 * stage_bytes<VT>(kSigmaMax);
+    grid = persistent_grid(kp, kThreads, stages, stages_max, p->num_sms);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    const size_t smem = add_hot_table<XT>(p, g, kp, stages, grid / p->num_sms);
+    if (smem != stages) grid = persistent_grid(kp, kThreads, smem, std::max(smem, stages_max), p->num_sms);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     if ((int64_t)grid > p->nb) grid = (int)p->nb;
     if (grid > kMaxParts) grid = kMaxParts;
-    kern<<<grid, kThreads, smem, st>>>(p->geom(), vals, x, epi);
+    kern<<<grid, kThreads, smem, st>>>(g, vals, x, epi);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int fgrid = (int)std::min<int64_t>((p->nb + 1 + 255) / 256, (int64_t)p->num_sms * 4);
-  merbit_finalize_kernel<Epi><<<fgrid, 256, 0, st>>>(p->geom(), epi, Epi::kReduce ? grid : 0);
+  merbit_finalize_kernel<Epi><<<fgrid, 256, 0, st>>>(g, epi, Epi::kReduce ? grid : 0);
   return cudaGetLastError();
 }
 

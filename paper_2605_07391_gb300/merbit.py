@@ -32,7 +32,7 @@ EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
            "merbit_spmv_noalloc_status",
            "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
-           "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
+           "merbit_plan_set_hot_columns", "merbit_gather_probe", "merbit_plan_set_wait_limit", "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
            "merbit_batch_get_plan", "merbit_batch_destroy", "merbit_autotune_sigma", "merbit_bicgstab",
            "merbit_last_error",
            "merbit_version"]
@@ -79,6 +79,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_plan_get_info": [vp, ctypes.POINTER(PlanInfo)],
             "merbit_plan_sync": [vp, vp],
             "merbit_plan_set_kernel": [vp, ctypes.c_int],
+            "merbit_gather_probe": [vp, i32, vp, vp, vp],
+            "merbit_plan_set_wait_limit": [vp, i32],
+            "merbit_plan_set_hot_columns": [vp, i32, dbl, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)],
             "merbit_plan_export": [vp, vp, vp, vp, vp],
             "merbit_spmv": [vp, i32, vp, vp, vp],
             "merbit_spmv_ex": [vp, i32, i32, vp, vp, vp, i32, vp],
@@ -215,6 +218,30 @@ class Plan:
     def set_kernel(self, kernel: str):
         """Block kernel for later products: "auto", "classic" or "split"."""
         _check("merbit_plan_set_kernel", load().merbit_plan_set_kernel(self.handle, KERNELS[kernel]))
+
+    def set_wait_limit(self, polls: int):
+        """merbit_plan_set_wait_limit (test aid): polls of a stage wait before it gives up;
+        -1 restores the default."""
+        _check("merbit_plan_set_wait_limit", load().merbit_plan_set_wait_limit(self.handle, int(polls)))
+
+    def set_hot_columns(self, max_hot: int, min_cover: float = 0.0, stream=None) -> tuple[int, float]:
+        """merbit_plan_set_hot_columns: (re)build the hot-column table (max_hot = 0 drops
+        it).  Returns (columns in the table, fraction of the nonzeros they hold)."""
+        n = ctypes.c_int(0)
+        cov = ctypes.c_double(0.0)
+        _check("merbit_plan_set_hot_columns", load().merbit_plan_set_hot_columns(
+            self.handle, int(max_hot), float(min_cover), _stream(stream), ctypes.byref(n), ctypes.byref(cov)))
+        return n.value, cov.value
+
+    def gather_probe(self, x: torch.Tensor, sink: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """merbit_gather_probe: one pass of the product's x gather alone (a timing aid);
+        returns the per-CTA sums (4096 entries of x's dtype)."""
+        _need_cuda(x, sink)
+        if sink is None:
+            sink = torch.zeros(4096, dtype=x.dtype, device=x.device)
+        _check("merbit_gather_probe", load().merbit_gather_probe(self.handle, _dt(x), _ptr(x), _ptr(sink),
+                                                                 _stream(stream)))
+        return sink
 
     def sync(self, stream=None):
         _check("merbit_plan_sync", load().merbit_plan_sync(self.handle, _stream(stream)))
