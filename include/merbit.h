@@ -92,7 +92,10 @@ merbit_status merbit_plan(const int32_t* row_ptr, const int32_t* col_idx, int64_
 
 /* As merbit_plan for an n_rows x n_cols matrix, with sigma in [1, 14]
  * (32-bit descriptors need 2*ceil(log2(32*sigma)) + sigma <= 32, Sec. 4.1.1),
- * tiles_per_block = 8, on `stream`. */
+ * tiles_per_block W in {4, 8, 16} (the block of W tiles that shares one
+ * shared-memory output buffer, Sec. 4.2; the block kernels keep 8 warps, one per
+ * tile for W = 8, warps idle past W = 4, two tiles per warp at W = 16; the SpMM and
+ * personalised PageRank need W = 8), on `stream`. */
 merbit_status merbit_plan_ex(const int32_t* row_ptr, const int32_t* col_idx, int64_t n_rows,
                              int64_t n_cols, int64_t nnz, int sigma, int tiles_per_block,
                              void* stream, merbit_plan_t* out);
@@ -119,13 +122,23 @@ merbit_status merbit_plan_export(merbit_plan_t plan, uint32_t* tile_x, uint32_t*
  *   MERBIT_KERNEL_SPLIT: 512 threads per CTA; 256 producer threads gather x and form
  *     the products of the next blocks while the 256 consumer threads reduce and
  *     commit the current one (three stages), so gathers and scans overlap.
+ *   MERBIT_KERNEL_SPLIT_COLS: the split kernel with stages of column indices only;
+ *     the producers read each value from global memory (coalesced, streamed past L1)
+ *     beside its gather and write the products over the column indices, which halves
+ *     the stages' shared memory and leaves L1 more room for x.  For values whose
+ *     products are 4 bytes wide (f32, bf16, f16); other value types use SPLIT.
+ *   MERBIT_KERNEL_SPLIT2: the split kernel with a ring of two stages instead of three
+ *     (less shared memory, so more L1 for x; the copy of block i + 2 then overlaps only
+ *     the producers' work on block i + 1).
  *   MERBIT_KERNEL_AUTO (the default): SPLIT for 32- and 64-bit values while two of
  *     its CTAs fit on an SM (its three stages at the plan's sigma), else CLASSIC;
  *     CLASSIC for 16-bit values (the faster choice in each case on sm_103a). */
 enum {
   MERBIT_KERNEL_AUTO = 0,
   MERBIT_KERNEL_CLASSIC = 1,
-  MERBIT_KERNEL_SPLIT = 2
+  MERBIT_KERNEL_SPLIT = 2,
+  MERBIT_KERNEL_SPLIT_COLS = 3,
+  MERBIT_KERNEL_SPLIT2 = 4
 };
 
 /* Choose the block kernel for every later call on this plan (host-side setting,
@@ -305,6 +318,25 @@ merbit_status merbit_autotune_sigma(const int32_t* row_ptr, const int32_t* col_i
                                     int64_t n_cols, int64_t nnz, merbit_dtype dtype, const void* vals,
                                     const int* candidates, int count, int reps, void* stream,
                                     int* best_sigma, float* ms_out);
+
+/*
+ * merbit_autotune — picks a plan's parameters for one matrix and value type by
+ * measurement: every combination of sigma (sigmas[n_sigma], each in [1, 14]), tiles per
+ * block (blocks[n_block], each 4, 8 or 16), block kernel (kernels[n_kernel], each a
+ * MERBIT_KERNEL_* value) and hot-column table size (hots[n_hot], each in [0, 2^20];
+ * merbit_plan_set_hot_columns with min_cover 0) is built and timed: one warm-up product
+ * and `reps` timed ones (CUDA events on `stream`, x = 0).  dtype is the value type (F32,
+ * F64, or BF16 / F16 with f32 vectors).  best (HOST, 4 ints) = {sigma, tiles_per_block,
+ * kernel, hot} of the fastest; ms_out (HOST, may be NULL, n_sigma * n_block * n_hot *
+ * n_kernel entries, row-major in that order) = mean milliseconds per product, -1 for a
+ * combination the device cannot launch.  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA
+ * (also when no combination can be launched), and those of merbit_plan_ex.
+ */
+merbit_status merbit_autotune(const int32_t* row_ptr, const int32_t* col_idx, int64_t n_rows,
+                              int64_t n_cols, int64_t nnz, merbit_dtype dtype, const void* vals,
+                              const int* sigmas, int n_sigma, const int* blocks, int n_block,
+                              const int* kernels, int n_kernel, const int* hots, int n_hot, int reps,
+                              void* stream, int* best, float* ms_out);
 
 /*
  * merbit_bicgstab — solves A x = b by unpreconditioned BiCGSTAB on the plan's SpMV (the

@@ -302,8 +302,8 @@ merbit_status merbit_plan_ex(const int32_t* row_ptr, const int32_t* col_idx, int
   if (nnz > 0 && !col_idx) return fail(MERBIT_EINVAL, "col_idx is NULL");
   if (sigma < 1 || sigma > kSigmaMax)
     return fail(MERBIT_EINVAL, "sigma must be in [1, %d] for 32-bit lane descriptors", kSigmaMax);
-  if (tiles_per_block != kTilesPerBlock)
-    return fail(MERBIT_EINVAL, "tiles_per_block must be %d", kTilesPerBlock);
+  if (tiles_per_block != 4 && tiles_per_block != 8 && tiles_per_block != kMaxW)
+    return fail(MERBIT_EINVAL, "tiles_per_block must be 4, 8 or 16");
   if (n_rows + nnz >= (int64_t)INT32_MAX)
     return fail(MERBIT_EOVERFLOW, "n_rows + nnz = %lld does not fit the int32 merge path",
                 (long long)(n_rows + nnz));
@@ -417,8 +417,8 @@ merbit_status merbit_plan_export(merbit_plan_t p, uint32_t* tile_x, uint32_t* ti
 
 merbit_status merbit_plan_set_kernel(merbit_plan_t p, int kernel) {
   if (merbit_status s = check_plan(p)) return s;
-  if (kernel < MERBIT_KERNEL_AUTO || kernel > MERBIT_KERNEL_SPLIT)
-    return fail(MERBIT_EINVAL, "kernel must be MERBIT_KERNEL_AUTO, _CLASSIC or _SPLIT");
+  if (kernel < MERBIT_KERNEL_AUTO || kernel > MERBIT_KERNEL_SPLIT2)
+    return fail(MERBIT_EINVAL, "kernel must be MERBIT_KERNEL_AUTO, _CLASSIC, _SPLIT, _SPLIT_COLS or _SPLIT2");
   p->spmv_kernel = kernel;
   return MERBIT_OK;
 }
@@ -484,6 +484,8 @@ merbit_status merbit_spmv(merbit_plan_t p, merbit_dtype dtype, const void* vals,
 merbit_status merbit_spmm(merbit_plan_t p, const float* vals, const float* X, float* Y, int64_t k,
                           int64_t ldx, int64_t ldy, void* stream) {
   if (merbit_status s = check_plan(p)) return s;
+  if (p->tiles_per_block != kTilesPerBlock)
+    return fail(MERBIT_EINVAL, "the SpMM needs a plan of %d tiles per block", kTilesPerBlock);
   if (k < 0 || ldx < k || ldy < k) return fail(MERBIT_EINVAL, "need k >= 0, ldx >= k, ldy >= k");
   if (k == 0 || p->n_rows == 0) return MERBIT_OK;
   if (!Y || (p->nnz > 0 && (!vals || !X))) return fail(MERBIT_EINVAL, "vals, X or Y is NULL");
@@ -501,6 +503,8 @@ merbit_status merbit_ppr(merbit_plan_t p, const float* vals, const int32_t* seed
                          double* resid_out, double* resid_hist, void* stream) {
   if (merbit_status s = check_plan(p)) return s;
   if (p->n_rows != p->n_cols) return fail(MERBIT_EINVAL, "personalised PageRank needs a square plan");
+  if (p->tiles_per_block != kTilesPerBlock)
+    return fail(MERBIT_EINVAL, "personalised PageRank needs a plan of %d tiles per block", kTilesPerBlock);
   if (!(alpha >= 0.0 && alpha < 1.0)) return fail(MERBIT_EINVAL, "alpha must be in [0, 1)");
   if (max_iter < 1) return fail(MERBIT_EINVAL, "max_iter must be >= 1");
   if (k < 1 || k > 1024) return fail(MERBIT_EINVAL, "k must be in [1, 1024]");

@@ -399,6 +399,9 @@ struct merbit_batch_s {
   cudaGraphExec_t exec = nullptr;
   merbit_dtype dt = MERBIT_F64;
   int spmv_kernel = -1;
+  const int32_t* hot_list = nullptr;   // the plan's hot-column table when recorded
+  const int32_t* col_hot = nullptr;
+  int hot_n = -1;
   const void* vals = nullptr;
   void* pi = nullptr;
   double alpha = -1.0, tol = -1.0;
@@ -625,7 +628,9 @@ merbit_status merbit_batch_pagerank(merbit_batch_t b, merbit_dtype dtype, const 
   const size_t es = dtype == MERBIT_F64 ? 8 : 4;
   cudaError_t e = cudaSuccess;
   const bool same = b->exec && b->dt == dtype && b->vals == vals && b->pi == pi && b->alpha == alpha &&
-                    b->tol == tol && b->max_iter == max_iter && b->spmv_kernel == b->plan->spmv_kernel;
+                    b->tol == tol && b->max_iter == max_iter && b->spmv_kernel == b->plan->spmv_kernel &&
+                    b->hot_list == b->plan->hot_list && b->col_hot == b->plan->col_hot &&
+                    b->hot_n == b->plan->hot_n;
   if (!same) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -657,6 +662,9 @@ merbit_status merbit_batch_pagerank(merbit_batch_t b, merbit_dtype dtype, const 
     b->tol = tol;
     b->max_iter = max_iter;
     b->spmv_kernel = b->plan->spmv_kernel;
+    b->hot_list = b->plan->hot_list;
+    b->col_hot = b->plan->col_hot;
+    b->hot_n = b->plan->hot_n;
   }
   e = cudaGraphLaunch(b->exec, st);
   std::vector<int> conv((size_t)b->G);

@@ -12,8 +12,11 @@ namespace merbit {
 
 constexpr int kOmega = 32;          // lanes per tile = warp size (Sec. 4.3)
 constexpr int kSigmaMax = 14;       // largest sigma of the 32-bit descriptor (Sec. 4.1.1)
-constexpr int kTilesPerBlock = 8;   // W: tiles that share one shared-memory output buffer
-constexpr int kThreads = kTilesPerBlock * kOmega;   // one warp per tile
+constexpr int kTilesPerBlock = 8;   // W: tiles that share one shared-memory output buffer (default)
+constexpr int kThreads = kTilesPerBlock * kOmega;   // block kernels: 8 warps, one per tile of W = 8
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxW = 16;           // largest W a plan may use (W in {4, 8, 16})
+constexpr int kMaxTpw = kMaxW / kWarps;             // tiles a warp reduces per block (at most)
 constexpr int kRedSlots = 64;       // spread slots of the grid-wide FP64 reductions
 constexpr uint32_t kMsb = 0x80000000u;
 constexpr uint32_t kSpinLimit = 1u << 22;           // bounded mbarrier waits
@@ -49,6 +52,8 @@ struct Geometry {
   int nnz;
   int steps;       // nnz + n_rows
   int sigma;
+  int W;           // tiles per block
+  int stages;      // split kernel: stages in its ring (2 or 3)
   int tile_num;
   int lane_num;
   int nb;          // number of blocks of tiles
@@ -101,7 +106,7 @@ struct merbit_plan_s {
     g.bnd_row = bnd_row; g.bnd_slot = bnd_slot;
     g.bnd_acc = bnd_acc; g.part = part; g.red = red;
     g.n_rows = (int)n_rows; g.nnz = (int)nnz; g.steps = (int)(nnz + n_rows);
-    g.sigma = sigma; g.tile_num = (int)tile_num; g.lane_num = (int)lane_num; g.nb = (int)nb;
+    g.sigma = sigma; g.W = tiles_per_block; g.stages = 3; g.tile_num = (int)tile_num; g.lane_num = (int)lane_num; g.nb = (int)nb;
     return g;
   }
 };
@@ -181,7 +186,8 @@ cudaError_t ir_apply(const merbit_plan_s* p, double* pi, double* s_out, cudaStre
 
 // Launch configuration of the split kernel's plain product (f32 or f64 values and
 // vectors) for a plan: grid, dynamic shared memory, geometry (with the hot-column table
-// if that launch takes it); false if it cannot be launched.
+// if that launch takes it); false if it cannot be launched.  For f32, a plan set to
+// MERBIT_KERNEL_SPLIT_COLS gives the column-only stages' configuration.
 bool split_config_f32(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem);
 bool split_config_f64(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem);
 

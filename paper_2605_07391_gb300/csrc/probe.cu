@@ -72,6 +72,19 @@ cudaError_t launch_probe(const merbit_plan_s* p, const XT* x, XT* sink, cudaStre
   if (!ok) return cudaErrorInvalidConfiguration;
   auto kern = gather_probe_kernel<XT>;
   const void* kp = reinterpret_cast<const void*>(kern);
+  // the probe needs fewer registers than the split kernel, so more of its CTAs could fit
+  // and the driver would pick a larger shared-memory carveout (a smaller L1) for it; ask
+  // for the carveout that the split kernel's resident CTAs need instead
+  int dev = 0, per_sm_total = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int per_sm = std::max(1, grid / p->num_sms);
+  if (per_sm_total > 0) {
+    const size_t need = (size_t)per_sm * (smem + (size_t)reserved + 1024);
+    const int pct = (int)std::min<size_t>(100, (need * 100 + per_sm_total - 1) / (size_t)per_sm_total);
+    cudaFuncSetAttribute(kp, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  }
   const int pgrid = persistent_grid(kp, kSplitThreads, smem, smem, p->num_sms);
   if (pgrid <= 0) return cudaErrorInvalidConfiguration;
   grid = std::min(grid, pgrid);

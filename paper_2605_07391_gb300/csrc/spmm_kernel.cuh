@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int G = gridDim.x;
   if (epi.skip(g.red)) return;
 
-  const size_t svb = stage_vals_bytes<float>(g.sigma);
-  const size_t stb = stage_bytes<float>(g.sigma);
+  const size_t svb = stage_vals_bytes<float>(g.sigma, kTilesPerBlock);
+  const size_t stb = stage_bytes<float>(g.sigma, kTilesPerBlock);
   auto sv = [&](int s) { return reinterpret_cast<float*>(dyn_smem + (size_t)s * stb); };
   auto sc = [&](int s) { return reinterpret_cast<int32_t*>(dyn_smem + (size_t)s * stb + svb); };
   const uint64_t pol_stream = policy_evict_first();
@@ -439,8 +439,8 @@ cudaError_t launch_spmm(const merbit_plan_s* p, const float* vals, const float* 
                         const SpmmGeometry& sg, const Epi& epi, cudaStream_t st) {
   if (p->nb == 0) return cudaSuccess;
   auto kern = merbit_spmm_kernel<KC, VW, Epi>;
-  const size_t smem = 2 * stage_bytes<float>(p->sigma);
-  const size_t smem_max = 2 * stage_bytes<float>(kSigmaMax);
+  const size_t smem = 2 * stage_bytes<float>(p->sigma, kTilesPerBlock);
+  const size_t smem_max = 2 * stage_bytes<float>(kSigmaMax, kTilesPerBlock);
   int grid = persistent_grid(reinterpret_cast<const void*>(kern), kThreads, smem, smem_max,
                              p->num_sms);
   if (grid <= 0) return cudaErrorInvalidConfiguration;

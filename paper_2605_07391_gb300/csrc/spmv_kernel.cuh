@@ -94,6 +94,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Bring [src, src + bytes) into L2 ahead of use (no shared-memory destination).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -309,25 +314,14 @@ struct StageInfo {
   int a0c, endc;                // column indices staged for [a0c, endc)
 };
 
+// Elements of a stage: the W * omega * sigma steps of a block (its nonzeros, then its row
+// sums) plus 32, since the lane scan may read up to 13 past the last product.
 template <typename VT>
-__host__ __device__ constexpr int stage_cap(int sigma) {
-  return kThreads * sigma + 32;   // the lane scan may read up to 13 past the last product
+__host__ __device__ constexpr int stage_cap(int sigma, int W) {
+  return W * kOmega * sigma + 32;
 }
 
 __host__ __device__ inline size_t round128(size_t b) { return (b + 127) & ~size_t(127); }
-
-template <typename VT>
-__host__ __device__ inline size_t stage_vals_bytes(int sigma) {
-  return round128(sizeof(VT) * (size_t)stage_cap<VT>(sigma));
-}
-template <typename VT>
-__host__ __device__ inline size_t stage_col_bytes(int sigma) {
-  return round128(sizeof(int32_t) * (size_t)stage_cap<VT>(sigma));
-}
-template <typename VT>
-__host__ __device__ inline size_t stage_bytes(int sigma) {
-  return stage_vals_bytes<VT>(sigma) + stage_col_bytes<VT>(sigma);
-}
 
 // A matrix whose stored values are all 1 (an adjacency pattern): no value stream is read
 // and a nonzero's product is x[col].  The type has the accumulator's width, so the
@@ -341,11 +335,55 @@ struct IsUnit : std::false_type {};
 template <typename AT>
 struct IsUnit<UnitVal<AT>> : std::true_type {};
 
-// Products go where an input of the same width was staged.
-template <typename VT, typename AT>
-struct ProdInVals {
-  static constexpr bool value = sizeof(VT) == sizeof(AT);
+// Stage layout.  VS: the values are staged by bulk copy beside the column indices (else
+// the producers read them from global memory, and the stage holds column indices only).
+// A stage has a value region when values are staged or the matrix is a pattern (the
+// region then holds the products); products go to the value region when it has their
+// width, otherwise over the column indices.
+template <typename VT, bool VS>
+struct HasValRegion {
+  static constexpr bool value = VS || IsUnit<VT>::value;
 };
+template <typename VT, typename AT, bool VS = true>
+struct ProdInVals {
+  static constexpr bool value = HasValRegion<VT, VS>::value && sizeof(VT) == sizeof(AT);
+};
+
+template <typename VT, bool VS = true>
+__host__ __device__ inline size_t stage_vals_bytes(int sigma, int W) {
+  return HasValRegion<VT, VS>::value ? round128(sizeof(VT) * (size_t)stage_cap<VT>(sigma, W)) : 0;
+}
+template <typename VT>
+__host__ __device__ inline size_t stage_col_bytes(int sigma, int W) {
+  return round128(sizeof(int32_t) * (size_t)stage_cap<VT>(sigma, W));
+}
+template <typename VT, bool VS = true>
+__host__ __device__ inline size_t stage_bytes(int sigma, int W) {
+  return stage_vals_bytes<VT, VS>(sigma, W) + stage_col_bytes<VT>(sigma, W);
+}
+
+// A value read from global memory by the producers (column-only stages): streamed once,
+// so it bypasses L1 and is marked evict-first in L2.
+__device__ __forceinline__ float ld_val(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_val(const double* p, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ __nv_bfloat16 ld_val(const __nv_bfloat16* p, uint64_t pol) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return __ushort_as_bfloat16(v);
+}
+__device__ __forceinline__ __half ld_val(const __half* p, uint64_t pol) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return __ushort_as_half(v);
+}
 
 // A block's coordinate range: nonzeros [xb, xe) and rows [yb, ye] (the tiles'
 // start coordinates of its first and one-past-last tile).
@@ -357,9 +395,10 @@ struct BlockSpan {
 // The shared-memory stages of a block kernel and the bulk copies that fill them.  Stage
 // s holds a block's values (none for UnitVal) and column indices; the products and the
 // block's row sums later overwrite them in place.
-template <typename VT, typename AT>
+template <typename VT, typename AT, bool VS = true>
 struct Stages {
   static constexpr int VE = 16 / (int)sizeof(VT);   // values per 16 bytes
+  static constexpr bool kStageVals = VS && !IsUnit<VT>::value;   // a value stream is copied
   const Geometry& g;
   const VT* vals;
   unsigned char* base;
@@ -368,7 +407,8 @@ struct Stages {
   uint64_t pol;       // L2 policy of the streams
 
   __device__ __forceinline__ Stages(const Geometry& g_, const VT* v, unsigned char* smem, uint64_t p)
-      : g(g_), vals(v), base(smem), svb(stage_vals_bytes<VT>(g_.sigma)), stb(stage_bytes<VT>(g_.sigma)),
+      : g(g_), vals(v), base(smem), svb(stage_vals_bytes<VT, VS>(g_.sigma, g_.W)),
+        stb(stage_bytes<VT, VS>(g_.sigma, g_.W)),
         nnz_v(g_.nnz & ~(VE - 1)), nnz_c(g_.nnz & ~3), pol(p) {}
 
   __device__ __forceinline__ VT* sv(int s) const { return reinterpret_cast<VT*>(base + (size_t)s * stb); }
@@ -377,8 +417,8 @@ struct Stages {
   }
 
   __device__ __forceinline__ BlockSpan span(int v) const {
-    const int bs = v * kTilesPerBlock;
-    const int be = min(bs + kTilesPerBlock, g.tile_num);
+    const int bs = v * g.W;
+    const int be = min(bs + g.W, g.tile_num);
     return BlockSpan{(int)g.tile_x[bs], (int)g.tile_x[be], g.tile_y[bs] & ~kMsb, g.tile_y[be] & ~kMsb};
   }
 
@@ -387,21 +427,27 @@ struct Stages {
     StageInfo in;
     in.x_bs = b.xb; in.x_be = b.xe; in.y_bs = (int)b.yb; in.y_be = (int)b.ye;
     in.a0v = b.xb & ~(VE - 1);
-    in.endv = max(in.a0v, min((b.xe + VE - 1) & ~(VE - 1), nnz_v));
+    in.endv = kStageVals ? max(in.a0v, min((b.xe + VE - 1) & ~(VE - 1), nnz_v)) : in.a0v;
     in.a0c = b.xb & ~3;
     in.endc = max(in.a0c, min((b.xe + 3) & ~3, nnz_c));
     *info = in;
-    const uint32_t bv = IsUnit<VT>::value ? 0u : (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT);
+    const uint32_t bv = kStageVals ? (uint32_t)(in.endv - in.a0v) * (uint32_t)sizeof(VT) : 0u;
     const uint32_t bc = (uint32_t)(in.endc - in.a0c) * 4u;
     mbar_arrive_expect_tx(bar, bv + bc);
     if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, bar, pol);
     if (bc) bulk_g2s(sc(s), g.col_stage + in.a0c, bc, bar, pol);
+    if constexpr (!kStageVals && !IsUnit<VT>::value) {
+      // the producers will read this block's values from global memory: start bringing
+      // them into L2 now, as far ahead as the column indices are copied
+      const int p0 = in.a0v, p1 = max(p0, min((b.xe + VE - 1) & ~(VE - 1), nnz_v));
+      if (p1 > p0) bulk_prefetch_l2(vals + p0, (uint32_t)(p1 - p0) * (uint32_t)sizeof(VT));
+    }
   }
 
   // The stage's product slots (over the values, or over the column indices for 16-bit
   // values) and the nonzero index of slot 0.
   __device__ __forceinline__ AT* prod(int s, const StageInfo& in, int& pb) const {
-    if constexpr (ProdInVals<VT, AT>::value) {
+    if constexpr (ProdInVals<VT, AT, VS>::value) {
       pb = in.a0v;
       return reinterpret_cast<AT*>(sv(s));
     } else {
@@ -423,11 +469,21 @@ struct Stages {
     ld_x_if(v, x + c, !hot, pol_x);
     xv = static_cast<AT>(v);
   }
+  // the value of nonzero k (1 for a pattern): staged, or read from global memory
+  __device__ __forceinline__ AT value(int s, const StageInfo& in, int k) const {
+    if constexpr (IsUnit<VT>::value) {
+      return AT(1);
+    } else if constexpr (kStageVals) {
+      return static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
+    } else {
+      return static_cast<AT>(widen(ld_val(vals + k, pol)));
+    }
+  }
   __device__ __forceinline__ AT product(int s, const StageInfo& in, int k, AT xv) const {
     if constexpr (IsUnit<VT>::value) {
       return xv;
     } else {
-      return static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k])) * xv;
+      return value(s, in, k) * xv;
     }
   }
 };
@@ -566,16 +622,21 @@ __global__ void __launch_bounds__(kThreads, 3)
     const int s = it & 1;
     const uint32_t par = (it >> 1) & 1;
 
-    // tile metadata of this warp, loaded before the wait to hide latency
-    const int ti = v * kTilesPerBlock + warp;
-    const bool tile_ok = ti < g.tile_num;
-    uint32_t txs = 0, txe = 0, tys = 0, desc = 0;
-    const int j = ti * kOmega + lane;
-    if (tile_ok) {
-      txs = __ldg(g.tile_x + ti);
-      txe = __ldg(g.tile_x + ti + 1);
-      tys = __ldg(g.tile_y + ti);
-      if (!(tys & kMsb) && j < g.lane_num) desc = ld_stream(g.lane_desc + j, pol_stream);
+    // tile metadata of this warp's tiles (warp, warp + 8 while < W), loaded before the
+    // wait to hide latency
+    uint32_t txs[kMaxTpw], txe[kMaxTpw], tys[kMaxTpw], desc[kMaxTpw];
+#pragma unroll
+    for (int t = 0; t < kMaxTpw; ++t) {
+      const int wt = warp + t * kWarps;
+      const int ti = v * g.W + wt;
+      const int j = ti * kOmega + lane;
+      txs[t] = txe[t] = tys[t] = desc[t] = 0;
+      if (wt < g.W && ti < g.tile_num) {
+        txs[t] = __ldg(g.tile_x + ti);
+        txe[t] = __ldg(g.tile_x + ti + 1);
+        tys[t] = __ldg(g.tile_y + ti);
+        if (!(tys[t] & kMsb) && j < g.lane_num) desc[t] = ld_stream(g.lane_desc + j, pol_stream);
+      }
     }
     // geometry for the copy issued at the end of this iteration
     BlockSpan next{0, 0, 0u, 0u};
@@ -597,17 +658,19 @@ __global__ void __launch_bounds__(kThreads, 3)
     // ---- stage products val * x[col] (load_smem of Algorithm MERBIT SpMV)
     {
       const int cnt = in.x_be - in.x_bs;
-      AT xv[kSigmaMax];
+      for (int base = 0; base < cnt; base += kThreads * kSigmaMax) {
+        AT xv[kSigmaMax];
 #pragma unroll
-      for (int u = 0; u < kSigmaMax; ++u) {
-        const int e = tid + u * kThreads;
-        xv[u] = AT(0);
-        if (e < cnt) st.gather(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
-      }
+        for (int u = 0; u < kSigmaMax; ++u) {
+          const int e = base + tid + u * kThreads;
+          xv[u] = AT(0);
+          if (e < cnt) st.gather(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
+        }
 #pragma unroll
-      for (int u = 0; u < kSigmaMax; ++u) {
-        const int e = tid + u * kThreads;
-        if (e < cnt) prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
+        for (int u = 0; u < kSigmaMax; ++u) {
+          const int e = base + tid + u * kThreads;
+          if (e < cnt) prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
+        }
       }
     }
     AT* s_y = prod + (in.x_be - pb);
@@ -615,10 +678,15 @@ __global__ void __launch_bounds__(kThreads, 3)
     __syncthreads();
 
     // ---- per-tile reduction (tile_fast_tackle / tile_normal_tackle + WarpSegmentedSum)
-    if (tile_ok && txs < txe) {
-      const int y_ws = (int)(tys & ~kMsb);
-      reduce_tile<AT>(g, prod + ((int)txs - pb), s_y + (y_ws - in.y_bs), txs, txe, tys, y_ws, desc, j,
-                      lane);
+#pragma unroll
+    for (int t = 0; t < kMaxTpw; ++t) {
+      // a tile without products (or past the block's or the path's last tile) adds nothing
+      if (txs[t] < txe[t]) {
+        const int ti = v * g.W + warp + t * kWarps;
+        const int y_ws = (int)(tys[t] & ~kMsb);
+        reduce_tile<AT>(g, prod + ((int)txs[t] - pb), s_y + (y_ws - in.y_bs), txs[t], txe[t], tys[t], y_ws,
+                        desc[t], ti * kOmega + lane, lane);
+      }
     }
     __syncthreads();
 
@@ -655,7 +723,7 @@ __global__ void __launch_bounds__(kThreads, 3)
 
 // ---------------------------------------------------------------- warp-specialized kernel
 // The same block reduction with the x gather split off: kSplitConsumers consumer threads
-// (each warp reduces kTilesPerBlock / (kSplitConsumers / 32) tiles of a block with the
+// (warp w reduces tiles w and w + 8 of a block, those below W, with the
 // per-tile reduction above) reduce and commit block i while kSplitProducers producer
 // threads gather x and form the products of blocks i + 1 and i + 2, so the SM's
 // load path stays busy through the scans instead of in per-block bursts.  Three stages
@@ -666,7 +734,7 @@ constexpr int kSplitConsumers = 256;
 constexpr int kSplitProducers = 256;
 constexpr int kSplitThreads = kSplitConsumers + kSplitProducers;
 constexpr int kSplitStages = 3;
-static_assert(kTilesPerBlock % (kSplitConsumers / 32) == 0, "whole tiles per consumer warp");
+static_assert(kSplitConsumers == kThreads, "a consumer warp takes the tiles a classic warp takes");
 
 // barrier 1 among the consumer threads only (warps 0 .. kSplitConsumers/32 - 1)
 __device__ __forceinline__ void consumers_sync() {
@@ -683,15 +751,17 @@ __device__ __forceinline__ bool consumers_or(bool pred) {
   return r != 0;
 }
 
-template <typename VT, typename XT, typename AT, typename Epi>
+template <typename VT, typename XT, typename AT, typename Epi, bool VS = true>
 __global__ void __launch_bounds__(kSplitThreads, 2)
     merbit_spmv_split_kernel(const Geometry g, const VT* __restrict__ vals, const XT* __restrict__ x,
                           Epi epi) {
-  static_assert(ProdInVals<VT, AT>::value || sizeof(AT) == 4, "product slot width");
-  constexpr int S = kSplitStages;
-  __shared__ __align__(8) uint64_t full[S];    // the stage's bulk copies have landed
-  __shared__ __align__(8) uint64_t ready[S];   // the stage's products are formed
-  __shared__ StageInfo info[S];
+  static_assert(ProdInVals<VT, AT, VS>::value || sizeof(AT) == 4, "product slot width");
+  using St = Stages<VT, AT, VS>;
+  constexpr bool kLoadVals = !St::kStageVals && !IsUnit<VT>::value;   // producers read the values
+  const int S = g.stages;                              // 2 or 3 stages in the ring
+  __shared__ __align__(8) uint64_t full[kSplitStages];   // the stage's bulk copies have landed
+  __shared__ __align__(8) uint64_t ready[kSplitStages];  // the stage's products are formed
+  __shared__ StageInfo info[kSplitStages];
   __shared__ double red_smem[kSplitConsumers / 32][2];
   __shared__ int failed;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -705,7 +775,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
 
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_x = policy_evict_last();
-  const Stages<VT, AT> st(g, vals, dyn_smem, pol_stream);
+  const St st(g, vals, dyn_smem, pol_stream);
   const BlockOrder<Epi> blk(g, epi);
   const int nbl = blk.n;
   // this CTA's blocks: blk(blockIdx.x + i * G) for i < nmine
@@ -755,16 +825,24 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       constexpr int NB = sizeof(AT) == 8 ? 10 : kSigmaMax;
       for (int base = 0; base < cnt; base += kSplitProducers * NB) {
         AT xv[NB];
+        AT wv[NB];   // values read from global memory (column-only stages)
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
           const int e = base + pt + u * kSplitProducers;
           xv[u] = AT(0);
-          if (e < cnt) st.gather(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
+          wv[u] = AT(0);
+          if (e < cnt) {
+            st.gather(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
+            if constexpr (kLoadVals) wv[u] = st.value(s, in, in.x_bs + e);
+          }
         }
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
           const int e = base + pt + u * kSplitProducers;
-          if (e < cnt) prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
+          if (e < cnt) {
+            if constexpr (kLoadVals) prod[in.x_bs + e - pb] = wv[u] * xv[u];
+            else prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
+          }
         }
       }
       AT* s_y = prod + (in.x_be - pb);
@@ -782,14 +860,14 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       const int kb = blockIdx.x + i * G;
       const int v = blk(kb);
       const int s = i % S;
-      constexpr int CW = kSplitConsumers / 32, TPW = kTilesPerBlock / CW;
+      constexpr int CW = kSplitConsumers / 32, TPW = kMaxTpw;
       uint32_t txs[TPW], txe[TPW], tys[TPW], desc[TPW];
 #pragma unroll
       for (int t = 0; t < TPW; ++t) {
-        const int ti = v * kTilesPerBlock + warp + t * CW;
+        const int ti = v * g.W + warp + t * CW;
         const int j = ti * kOmega + lane;
         txs[t] = txe[t] = tys[t] = desc[t] = 0;
-        if (ti < g.tile_num) {
+        if (warp + t * CW < g.W && ti < g.tile_num) {
           txs[t] = __ldg(g.tile_x + ti);
           txe[t] = __ldg(g.tile_x + ti + 1);
           tys[t] = __ldg(g.tile_y + ti);
@@ -816,7 +894,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       for (int t = 0; t < TPW; ++t) {
         // a tile without products (or past the last tile) adds nothing
         if (txs[t] < txe[t]) {
-          const int ti = v * kTilesPerBlock + warp + t * CW;
+          const int ti = v * g.W + warp + t * CW;
           const int y_ws = (int)(tys[t] & ~kMsb);
           reduce_tile<AT>(g, prod + ((int)txs[t] - pb), s_y + (y_ws - in.y_bs), txs[t], txe[t], tys[t],
                           y_ws, desc[t], ti * kOmega + lane, lane);
@@ -880,6 +958,11 @@ __device__ __forceinline__ void grid_sum2(double p0, double p1, RedState* red, F
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
       a += red_smem[w][0];
       b += red_smem[w][1];
+    }
+    if (gridDim.x == 1) {
+      // a single CTA holds the whole sum: no spread slots, fence or arrival count
+      finish(a, b);
+      return;
     }
     const int q = blockIdx.x % kRedSlots;
     atomicAdd(&red->slot[q][0], a);
@@ -946,12 +1029,13 @@ inline size_t add_hot_table(const merbit_plan_s* p, Geometry& g, const void* ker
 // Grid, dynamic shared memory and geometry (with or without the hot-column table) of the
 // split kernel's launch for a plan; false if two of its CTAs do not fit on an SM (or
 // none does, when `forced`).
-template <typename VT, typename XT, typename AT, typename Epi>
+template <typename VT, typename XT, typename AT, typename Epi, bool VS>
 bool split_config(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem, bool forced) {
-  auto kern = merbit_spmv_split_kernel<VT, XT, AT, Epi>;
+  auto kern = merbit_spmv_split_kernel<VT, XT, AT, Epi, VS>;
   const void* kp = reinterpret_cast<const void*>(kern);
-  const size_t stages = kSplitStages * stage_bytes<VT>(p->sigma);
-  const size_t stages_max = kSplitStages * stage_bytes<VT>(kSigmaMax);
+  g.stages = p->spmv_kernel == MERBIT_KERNEL_SPLIT2 ? 2 : kSplitStages;
+  const size_t stages = (size_t)g.stages * stage_bytes<VT, VS>(p->sigma, p->tiles_per_block);
+  const size_t stages_max = stages;
   grid = persistent_grid(kp, kSplitThreads, stages, stages_max, p->num_sms);
   if (grid <= 0 || (!forced && grid < 2 * p->num_sms)) return false;
   smem = add_hot_table<XT>(p, g, kp, stages, grid / p->num_sms);
@@ -972,20 +1056,33 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   Geometry g = p->geom();
   int grid = 0;
   bool split = false;
-  if (p->spmv_kernel == MERBIT_KERNEL_SPLIT ||
-      (p->spmv_kernel == MERBIT_KERNEL_AUTO && sizeof(VT) >= 4)) {
+  // column-only stages need 4-byte products (they are written over the column indices)
+  constexpr bool kColsOk = sizeof(AT) == 4 && !IsUnit<VT>::value;
+  const int kind = p->spmv_kernel;
+  if constexpr (kColsOk) {
+    if (kind == MERBIT_KERNEL_SPLIT_COLS) {
+      size_t smem = 0;
+      split = split_config<VT, XT, AT, Epi, false>(p, g, grid, smem, true);
+      if (!split) return cudaErrorInvalidConfiguration;
+      merbit_spmv_split_kernel<VT, XT, AT, Epi, false><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
+    }
+  }
+  if (split) {
+    // launched above
+  } else if (kind == MERBIT_KERNEL_SPLIT || kind == MERBIT_KERNEL_SPLIT_COLS || kind == MERBIT_KERNEL_SPLIT2 ||
+             (kind == MERBIT_KERNEL_AUTO && sizeof(VT) >= 4)) {
     size_t smem = 0;
-    const bool forced = p->spmv_kernel == MERBIT_KERNEL_SPLIT;
-    split = split_config<VT, XT, AT, Epi>(p, g, grid, smem, forced);
+    const bool forced = kind != MERBIT_KERNEL_AUTO;
+    split = split_config<VT, XT, AT, Epi, true>(p, g, grid, smem, forced);
     if (!split && forced) return cudaErrorInvalidConfiguration;
-    if (split) merbit_spmv_split_kernel<VT, XT, AT, Epi><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
+    if (split) merbit_spmv_split_kernel<VT, XT, AT, Epi, true><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
   }
   if (!split) {
     g = p->geom();
     auto kern = merbit_spmv_kernel<VT, XT, AT, Epi>;
     const void* kp = reinterpret_cast<const void*>(kern);
-    const size_t stages = 2 * stage_bytes<VT>(p->sigma);
-    const size_t stages_max = 2 * stage_bytes<VT>(kSigmaMax);
+    const size_t stages = 2 * stage_bytes<VT>(p->sigma, p->tiles_per_block);
+    const size_t stages_max = stages;
     grid = persistent_grid(kp, kThreads, stages, stages_max, p->num_sms);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     const size_t smem = add_hot_table<XT>(p, g, kp, stages, grid / p->num_sms);

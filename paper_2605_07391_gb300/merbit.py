@@ -21,7 +21,7 @@ F32, F64, BF16, F16 = 0, 1, 2, 3
 PLAIN, IR_BF16, IR_F16, IR_F32 = 0, 1, 2, 3
 STATUS = {0: "OK", 1: "EINVAL", 2: "EOVERFLOW", 3: "ENOMEM", 4: "ECUDA", 5: "ENOTCONV",
           6: "EDEVICE"}
-KERNELS = {"auto": 0, "classic": 1, "split": 2}
+KERNELS = {"auto": 0, "classic": 1, "split": 2, "split_cols": 3, "split2": 4}
 MODES = {"plain": PLAIN, "ir_bf16": IR_BF16, "ir_f16": IR_F16, "ir_f32": IR_F32}
 _TORCH_DT = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch.float16: F16}
 
@@ -32,7 +32,8 @@ EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_
            "merbit_vals_convert", "merbit_pagerank", "merbit_pagerank_ex", "merbit_spmv_noalloc",
            "merbit_spmv_noalloc_status",
            "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
-           "merbit_plan_set_hot_columns", "merbit_gather_probe", "merbit_plan_set_wait_limit", "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
+           "merbit_plan_set_hot_columns", "merbit_gather_probe", "merbit_plan_set_wait_limit",
+           "merbit_autotune", "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
            "merbit_batch_get_plan", "merbit_batch_destroy", "merbit_autotune_sigma", "merbit_bicgstab",
            "merbit_last_error",
            "merbit_version"]
@@ -105,6 +106,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_batch_pagerank": [vp, i32, vp, dbl, dbl, i32, vp, vp, vp, ctypes.POINTER(i32), vp],
             "merbit_autotune_sigma": [vp, vp, i64, i64, i64, i32, vp, vp, i32, i32, vp,
                                       ctypes.POINTER(i32), vp],
+            "merbit_autotune": [vp, vp, i64, i64, i64, i32, vp, vp, i32, vp, i32, vp, i32, vp, i32, i32,
+                                vp, vp, vp],
             "merbit_spmv_noalloc": [vp, vp, vp, vp, vp, i64, i64, i64, vp],
             "merbit_spmv_noalloc_status": [vp],
             "merbit_bicgstab": [vp, vp, vp, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl),
@@ -336,10 +339,19 @@ class Batch:
         return self._handle
 
     def set_kernel(self, kernel: str):
-        """Block kernel of the batch's plan: "auto", "classic" or "split" (the solve is
-        recorded again at the next call)."""
+        """Block kernel of the batch's plan: "auto", "classic", "split" or "split_cols" (the
+        solve is recorded again at the next call)."""
         h = ctypes.c_void_p(load().merbit_batch_get_plan(self.handle))
         _check("merbit_plan_set_kernel", load().merbit_plan_set_kernel(h, KERNELS[kernel]))
+
+    def set_hot_columns(self, max_hot: int, min_cover: float = 0.0, stream=None) -> tuple[int, float]:
+        """Hot-column table of the batch's plan (the solve is recorded again at the next call)."""
+        h = ctypes.c_void_p(load().merbit_batch_get_plan(self.handle))
+        n = ctypes.c_int(0)
+        cov = ctypes.c_double(0.0)
+        _check("merbit_plan_set_hot_columns", load().merbit_plan_set_hot_columns(
+            h, int(max_hot), float(min_cover), _stream(stream), ctypes.byref(n), ctypes.byref(cov)))
+        return n.value, cov.value
 
     def plan_info(self) -> PlanInfo:
         """merbit_plan_get_info of the batch's plan (owned by the batch)."""
@@ -391,6 +403,35 @@ def autotune_sigma(row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Ten
         cand.ctypes.data_as(ctypes.c_void_p), cand.size, reps, _stream(stream), ctypes.byref(best),
         ms.ctypes.data_as(ctypes.c_void_p)))
     return best.value, {int(c): float(t) for c, t in zip(cand, ms)}
+
+
+def autotune(row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor,
+             n_rows: int | None = None, n_cols: int | None = None, sigmas=(14, 12, 10),
+             blocks=(8,), kernels=("auto",), hots=(0,), reps: int = 5, stream=None) -> tuple[dict, dict]:
+    """merbit_autotune: the fastest (sigma, tiles_per_block, kernel, hot) for this matrix and
+    value type.  Returns (best, {(sigma, W, kernel, hot): ms per product or None})."""
+    _need_cuda(row_ptr, col_idx, vals)
+    n_rows = row_ptr.numel() - 1 if n_rows is None else n_rows
+    n_cols = n_rows if n_cols is None else n_cols
+    arr = [np.ascontiguousarray(np.asarray(v, dtype=np.int32)) for v in
+           (sigmas, blocks, [KERNELS[k] for k in kernels], hots)]
+    ms = np.zeros(int(np.prod([a.size for a in arr])), np.float32)
+    best = np.zeros(4, np.int32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check("merbit_autotune", load().merbit_autotune(
+        _ptr(row_ptr), _ptr(col_idx), n_rows, n_cols, col_idx.numel(), _dt(vals), _ptr(vals),
+        vp(arr[0]), arr[0].size, vp(arr[1]), arr[1].size, vp(arr[2]), arr[2].size, vp(arr[3]), arr[3].size,
+        reps, _stream(stream), vp(best), vp(ms)))
+    names = {v: k for k, v in KERNELS.items()}
+    table, i = {}, 0
+    for s_ in sigmas:
+        for b in blocks:
+            for h in hots:
+                for k in kernels:
+                    table[(int(s_), int(b), k, int(h))] = float(ms[i]) if ms[i] > 0 else None
+                    i += 1
+    return ({"sigma": int(best[0]), "tiles_per_block": int(best[1]), "kernel": names[int(best[2])],
+             "hot": int(best[3])}, table)
 
 
 def bicgstab(p: "Plan", vals: torch.Tensor | None, b: torch.Tensor, x: torch.Tensor | None = None,
@@ -462,9 +503,10 @@ def pagerank_adjoint(p: "Plan", pt: "Plan", vals_t: torch.Tensor, w: torch.Tenso
     return lam, {"iters": iters.value, "resid": resid.value, "converged": st == 0}
 
 
-def plan(row_ptr, col_idx, n_rows=None, n_cols=None, sigma=14, stream=None) -> Plan:
-    """merbit_plan: build the reusable TILE schedule of a CSR pattern."""
-    return Plan(row_ptr, col_idx, n_rows, n_cols, sigma=sigma, stream=stream)
+def plan(row_ptr, col_idx, n_rows=None, n_cols=None, sigma=14, stream=None, tiles_per_block=8) -> Plan:
+    """merbit_plan_ex: build the reusable TILE schedule of a CSR pattern."""
+    return Plan(row_ptr, col_idx, n_rows, n_cols, sigma=sigma, tiles_per_block=tiles_per_block,
+                stream=stream)
 
 
 def spmv(p: Plan, vals: torch.Tensor, x: torch.Tensor, y: torch.Tensor | None = None,

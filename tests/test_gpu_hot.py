@@ -69,7 +69,7 @@ def test_selection_rule_exact(cuda_device, max_hot):
     assert p.set_hot_columns(0) == (0, 0.0)
 
 
-@pytest.mark.parametrize("kernel", ["split", "classic"])
+@pytest.mark.parametrize("kernel", ["split", "split_cols", "split2", "classic"])
 @pytest.mark.parametrize("sigma", [14, 10, 7])
 def test_spmv_with_table_both_kernels(cuda_device, kernel, sigma):
     a = inputs.add_hubs(inputs.rmat_uniform(16, 16, 3, 3), 2, 20000, 40000, 5)
@@ -116,7 +116,7 @@ def test_degenerate_tables(cuda_device):
     p, _ = _plan(a)
     n, cover = p.set_hot_columns(16)
     assert n == 3 and cover == 1.0
-    for kernel in ("split", "classic"):
+    for kernel in ("split", "split_cols", "split2", "classic"):
         p.set_kernel(kernel)
         _spmv_check(p, a, torch.float32, what=f"three columns {kernel}")
     # every column used once: no column qualifies
@@ -150,12 +150,13 @@ def test_full_rmat24_f32_with_table(cuda_device):
     _spmv_check(p, a, torch.float32, what="rmat24 f32 with table")
 
 
+@pytest.mark.parametrize("kernel", ["split", "split_cols"])
 @pytest.mark.parametrize("max_hot", [0, 3000])
-def test_gather_probe_sums_every_gather(cuda_device, max_hot):
+def test_gather_probe_sums_every_gather(cuda_device, max_hot, kernel):
     """The gather probe loads x[col[k]] once per nonzero (from the table for hot columns):
     its per-CTA sums add up to sum_c uses(c) x[c]."""
     a = inputs.rmat_uniform(16, 16, 3, 3)
-    p, _ = _plan(a)
+    p, _ = _plan(a, 14, kernel)
     p.set_hot_columns(max_hot)
     cnt = np.bincount(a.col, minlength=a.n_cols).astype(np.float64)
     for dtype, tol in ((torch.float32, 1e-5), (torch.float64, 1e-12)):
