@@ -56,9 +56,24 @@ def tile_counts(n: int, m: int, sigma: int, omega: int = OMEGA) -> tuple[int, in
     return -(-steps // (omega * sigma)), -(-steps // sigma)
 
 
-def descriptor_fits(sigma: int, omega: int = OMEGA) -> bool:
-    """32-bit descriptor condition 2*ceil(log2(omega*sigma)) + sigma <= 32 (Sec. 4.1.1)."""
-    return 2 * math.ceil(math.log2(omega * sigma)) + sigma <= 32
+def descriptor_fits(sigma: int, omega: int = OMEGA, bits: int = 32) -> bool:
+    """Descriptor condition 2*ceil(log2(omega*sigma)) + sigma <= bits (Sec. 4.1.1 states it
+    for a 32-bit word; Sec. 5.3.4 names the 64-bit word as the way to larger sigma)."""
+    return 2 * math.ceil(math.log2(omega * sigma)) + sigma <= bits
+
+
+def descriptor_layout(sigma: int, omega: int = OMEGA) -> tuple[int, int]:
+    """(word bits, offset field width) of the lane descriptor for a sigma.
+
+    sigma <= 14: the paper's 32-bit word with 9-bit offset fields (flag<<18 | y<<9 | x).
+    15 <= sigma <= 42: a 64-bit word with 11-bit offset fields (flag<<22 | y<<11 | x); 11
+    bits hold offsets below omega*sigma <= 1344 and 22 + sigma <= 64 bits hold the flags.
+    """
+    if sigma >= 1 and sigma <= 14 and descriptor_fits(sigma, omega) and omega * sigma <= 512:
+        return 32, 9
+    if 15 <= sigma <= 42 and omega * sigma <= 2048 and 22 + sigma <= 64:
+        return 64, 11
+    raise ValueError("lane descriptors cover sigma in [1, 42] (32-bit up to 14, 64-bit above)")
 
 
 def merge_path_down_steps(row_ptr: np.ndarray) -> np.ndarray:
@@ -84,12 +99,12 @@ def build_tile(row_ptr: np.ndarray, sigma: int, omega: int = OMEGA) -> dict:
     is (number of right steps, number of down steps) before step j*sigma.  Tile
     i = lanes [i*omega, (i+1)*omega) starts where its lane 0 starts.  Offsets
     are lane start minus tile start; lane_desc = bit_flag<<18 | y_off<<9 |
-    x_off; tile_y gets its most significant bit set when the tile has no down
+    x_off (a 64-bit word bit_flag<<22 | y_off<<11 | x_off for sigma > 14,
+    descriptor_layout); tile_y gets its most significant bit set when the tile has no down
     step at all (a single-row tile, Sec. 4.1.2 step (3)).  The last entry of
     tile_x / tile_y is (m, n).
     """
-    if not descriptor_fits(sigma, omega) or omega * sigma > 512 or sigma > 14:
-        raise ValueError("32-bit lane descriptor needs sigma <= 14 and omega*sigma <= 512")
+    bits, w = descriptor_layout(sigma, omega)
     row_ptr = np.asarray(row_ptr, np.int64)
     n = row_ptr.size - 1
     m = int(row_ptr[-1])
@@ -117,7 +132,7 @@ def build_tile(row_ptr: np.ndarray, sigma: int, omega: int = OMEGA) -> dict:
         idx = np.where(valid, start + k, 0)
         bit = valid & down[idx] if steps else np.zeros(lane_num, bool)
         flags |= bit.astype(np.int64) << k
-    desc = (flags << 18) | (y_off << 9) | x_off
+    desc = (flags << (2 * w)) | (y_off << w) | x_off
 
     tile_end = np.minimum((np.arange(tile_num, dtype=np.int64) + 1) * omega * sigma, steps)
     tile_begin = np.arange(tile_num, dtype=np.int64) * omega * sigma
@@ -130,21 +145,23 @@ def build_tile(row_ptr: np.ndarray, sigma: int, omega: int = OMEGA) -> dict:
         "lane_num": lane_num,
         "tile_x": np.concatenate([tx, [m]]).astype(np.uint32),
         "tile_y": np.concatenate([tile_y, np.array([n], np.uint32)]).astype(np.uint32),
-        "lane_desc": desc.astype(np.uint32),
+        "lane_desc": desc.astype(np.uint32 if bits == 32 else np.uint64),
     }
 
 
-def decode_lane_desc(desc: int) -> tuple[int, int, int]:
-    """(x_offset, y_offset, bit_flag) of a 32-bit lane descriptor (Sec. 4.1.1)."""
+def decode_lane_desc(desc: int, sigma: int = 14) -> tuple[int, int, int]:
+    """(x_offset, y_offset, bit_flag) of a lane descriptor (Sec. 4.1.1)."""
     desc = int(desc)
-    return desc & 0x1FF, (desc >> 9) & 0x1FF, desc >> 18
+    _, w = descriptor_layout(sigma)
+    mask = (1 << w) - 1
+    return desc & mask, (desc >> w) & mask, desc >> (2 * w)
 
 
-def step_coordinate(tile_start: tuple[int, int], desc: int, k: int) -> tuple[int, int]:
+def step_coordinate(tile_start: tuple[int, int], desc: int, k: int, sigma: int = 14) -> tuple[int, int]:
     """Coordinate reached after the first k steps of a lane (Sec. 4.1.1):
     (tile_x + x_offset + k_x, tile_y + y_offset + k_y), where k_y counts the set
     bits among the first k bits of bit_flag and k_x = k - k_y."""
-    xo, yo, flags = decode_lane_desc(desc)
+    xo, yo, flags = decode_lane_desc(desc, sigma)
     k_y = bin(flags & ((1 << k) - 1)).count("1")
     return tile_start[0] + xo + (k - k_y), tile_start[1] + yo + k_y
 

@@ -55,10 +55,20 @@ def test_descriptor_fit_condition():
     assert oracle.descriptor_fits(14) and oracle.descriptor_fits(7)
     assert not oracle.descriptor_fits(15)
     assert 2 * math.ceil(math.log2(32 * 14)) + 14 == 32
+    # the 64-bit word (Sec. 5.3.4): 2 * 11 offset bits + sigma flag bits, sigma up to 42
+    assert oracle.descriptor_fits(42, bits=64) and not oracle.descriptor_fits(43, bits=64)
+    assert oracle.descriptor_layout(14) == (32, 9) and oracle.descriptor_layout(15) == (64, 11)
+    assert oracle.descriptor_layout(42) == (64, 11)
+    for bad in (0, 43):
+        with pytest.raises(ValueError):
+            oracle.descriptor_layout(bad)
 
 
 def _walk_tile(row_ptr, sigma, omega):
-    """Literal merge-path walk of Sec. 4.1.2: one step at a time, plain Python."""
+    """Literal merge-path walk of Sec. 4.1.2: one step at a time, plain Python.  The
+    descriptor packs bit_flag, y_off, x_off with 9-bit offset fields up to sigma = 14 (the
+    32-bit word of Sec. 4.1.1) and 11-bit fields above (the 64-bit word)."""
+    w = 9 if sigma <= 14 else 11
     row_ptr = [int(v) for v in row_ptr]
     n, m = len(row_ptr) - 1, row_ptr[-1]
     total = m + n
@@ -89,7 +99,7 @@ def _walk_tile(row_ptr, sigma, omega):
             s = j * sigma + k
             if s < total and downs[s]:
                 f |= 1 << k
-        desc.append((f << 18) | ((ly - sy) << 9) | (lx - sx))
+        desc.append((f << (2 * w)) | ((ly - sy) << w) | (lx - sx))
     return tile_x + [m], tile_y + [n], desc
 
 
@@ -104,13 +114,13 @@ CASES = [
 
 
 @pytest.mark.parametrize("name,row_ptr", CASES)
-@pytest.mark.parametrize("sigma", [14, 7, 4, 1])
+@pytest.mark.parametrize("sigma", [14, 7, 4, 1, 15, 28, 42])
 def test_build_tile_matches_walk_special(name, row_ptr, sigma):
     _check_against_walk(np.asarray(row_ptr, np.int64), sigma)
 
 
 @pytest.mark.parametrize("seed", range(6))
-@pytest.mark.parametrize("sigma", [14, 7, 3])
+@pytest.mark.parametrize("sigma", [14, 7, 3, 17, 42])
 def test_build_tile_matches_walk_random(seed, sigma):
     a = inputs.random_sparse(300 + 37 * seed, 200, 0.03 * (seed + 1), seed, empty_frac=0.3)
     _check_against_walk(a.row_ptr, sigma)
@@ -147,7 +157,7 @@ def _walk_block_rows(row_ptr, sigma, omega, W):
 
 
 @pytest.mark.parametrize("W", [8, 4, 16, 3])
-@pytest.mark.parametrize("sigma", [14, 7, 2])
+@pytest.mark.parametrize("sigma", [14, 7, 2, 28])
 @pytest.mark.parametrize("case", range(5))
 def test_block_boundary_rows_match_walk(case, sigma, W):
     if case < 3:
@@ -163,13 +173,15 @@ def test_block_boundary_rows_match_walk(case, sigma, W):
     assert got.tolist() == _walk_block_rows(row_ptr, sigma, 32, W)
 
 
-def test_build_tile_invariants_rmat14():
+@pytest.mark.parametrize("sigma", [14, 28])
+def test_build_tile_invariants_rmat14(sigma):
     a = inputs.rmat_transition(14, 16, 1)
-    sigma = 14
     t = oracle.build_tile(a.row_ptr, sigma)
-    desc = t["lane_desc"].astype(np.int64)
-    flags = desc >> 18
-    xo, yo = desc & 511, (desc >> 9) & 511
+    w = 9 if sigma <= 14 else 11
+    desc = t["lane_desc"].astype(np.uint64)
+    flags = desc >> np.uint64(2 * w)
+    xo = (desc & np.uint64((1 << w) - 1)).astype(np.int64)
+    yo = ((desc >> np.uint64(w)) & np.uint64((1 << w) - 1)).astype(np.int64)
     pop = np.array([bin(int(f)).count("1") for f in flags])
     assert pop.sum() == a.n_rows                        # one down step per row
     total = a.nnz + a.n_rows
