@@ -74,6 +74,10 @@ typedef struct merbit_plan_info {
   const uint32_t* lane_desc;/* device, lane_num: bit_flag<<18 | y_off<<9 | x_off */
   const int32_t* block_row; /* device, block_num + 1: row of each block's first
                                coordinate (ROW(tile_y[b * W])); last = n_rows    */
+  int32_t desc_bytes;       /* 4: lane_desc holds 32-bit words (sigma <= 14);
+                               8: 64-bit words bit_flag<<22 | y_off<<11 | x_off
+                               (sigma 15..42; the pointer above then addresses
+                               lane_num 64-bit words)                            */
 } merbit_plan_info;
 
 /*
@@ -90,8 +94,11 @@ typedef struct merbit_plan_info {
 merbit_status merbit_plan(const int32_t* row_ptr, const int32_t* col_idx, int64_t n,
                           int64_t nnz, merbit_plan_t* out);
 
-/* As merbit_plan for an n_rows x n_cols matrix, with sigma in [1, 14]
- * (32-bit descriptors need 2*ceil(log2(32*sigma)) + sigma <= 32, Sec. 4.1.1),
+/* As merbit_plan for an n_rows x n_cols matrix, with sigma in [1, 42]
+ * (32-bit descriptors need 2*ceil(log2(32*sigma)) + sigma <= 32, Sec. 4.1.1, so
+ * sigma <= 14; sigma 15..42 uses 64-bit descriptors bit_flag<<22 | y_off<<11 | x_off,
+ * the larger word Sec. 5.3.4 names; those plans serve the SpMV and the solvers built on
+ * it, not the SpMM, personalised PageRank or batches),
  * tiles_per_block W in {4, 8, 16} (the block of W tiles that shares one
  * shared-memory output buffer, Sec. 4.2; the block kernels keep 8 warps, one per
  * tile for W = 8, warps idle past W = 4, two tiles per warp at W = 16; the SpMM and
@@ -108,7 +115,8 @@ void merbit_plan_destroy(merbit_plan_t plan);
 merbit_status merbit_plan_get_info(merbit_plan_t plan, merbit_plan_info* info);
 
 /* Copy the TILE arrays and block rows to HOST buffers (sizes as in
- * merbit_plan_info: tile_num + 1, tile_num + 1, lane_num, block_num + 1);
+ * merbit_plan_info: tile_num + 1, tile_num + 1, lane_num words of desc_bytes each,
+ * block_num + 1);
  * any pointer may be NULL to skip that array.  Synchronous (device-wide).
  * Errors: EINVAL, ECUDA. */
 merbit_status merbit_plan_export(merbit_plan_t plan, uint32_t* tile_x, uint32_t* tile_y,
@@ -130,6 +138,8 @@ merbit_status merbit_plan_export(merbit_plan_t plan, uint32_t* tile_x, uint32_t*
  *   MERBIT_KERNEL_SPLIT2: the split kernel with a ring of two stages instead of three
  *     (less shared memory, so more L1 for x; the copy of block i + 2 then overlaps only
  *     the producers' work on block i + 1).
+ *   A split kernel that cannot hold one CTA's stages on an SM (large sigma x block
+ *   size with 8-byte values) gives way to CLASSIC.
  *   MERBIT_KERNEL_AUTO (the default): SPLIT for 32- and 64-bit values while two of
  *     its CTAs fit on an SM (its three stages at the plan's sigma), else CLASSIC;
  *     CLASSIC for 16-bit values (the faster choice in each case on sm_103a). */
@@ -163,6 +173,20 @@ merbit_status merbit_plan_set_kernel(merbit_plan_t plan, int kernel);
  */
 merbit_status merbit_plan_set_hot_columns(merbit_plan_t plan, int max_hot, double min_cover,
                                           void* stream, int* hot_n_out, double* cover_out);
+
+/*
+ * merbit_plan_set_cold_columns — mark the columns referenced by at most max_uses nonzeros
+ * (0 clears the marks) in the plan's tagged copy of col_idx (the copy of
+ * merbit_plan_set_hot_columns, rebuilt here with the plan's current table settings): the
+ * products gather x at those columns without allocating them in L1, so the lines of x
+ * that are used again stay there.  No counterpart in the paper (a GB300 choice for the x
+ * gather of Sec. 4.2).  Only for n_cols <= 2^30 (bit 30 of a column index carries the
+ * mark); otherwise nothing is marked.  Products are unchanged.  *cover_out (host, may be
+ * NULL) = the fraction of the nonzeros in marked columns.  Synchronises `stream`.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+merbit_status merbit_plan_set_cold_columns(merbit_plan_t plan, int max_uses, void* stream,
+                                           double* cover_out);
 
 /*
  * merbit_gather_probe — a measurement aid with no counterpart in the paper: one pass of

@@ -300,8 +300,9 @@ merbit_status merbit_plan_ex(const int32_t* row_ptr, const int32_t* col_idx, int
   if (n_rows < 0 || n_cols < 0 || nnz < 0) return fail(MERBIT_EINVAL, "negative size");
   if (!row_ptr) return fail(MERBIT_EINVAL, "row_ptr is NULL");
   if (nnz > 0 && !col_idx) return fail(MERBIT_EINVAL, "col_idx is NULL");
-  if (sigma < 1 || sigma > kSigmaMax)
-    return fail(MERBIT_EINVAL, "sigma must be in [1, %d] for 32-bit lane descriptors", kSigmaMax);
+  if (sigma < 1 || sigma > kSigmaMax64)
+    return fail(MERBIT_EINVAL, "sigma must be in [1, %d] (32-bit lane descriptors up to %d, 64-bit above)",
+                kSigmaMax64, kSigmaMax);
   if (tiles_per_block != 4 && tiles_per_block != 8 && tiles_per_block != kMaxW)
     return fail(MERBIT_EINVAL, "tiles_per_block must be 4, 8 or 16");
   if (n_rows + nnz >= (int64_t)INT32_MAX)
@@ -335,6 +336,7 @@ merbit_status merbit_plan_ex(const int32_t* row_ptr, const int32_t* col_idx, int
   p->n_cols = n_cols;
   p->nnz = nnz;
   p->sigma = sigma;
+  p->desc_bytes = sigma > kSigmaMax ? 8 : 4;
   p->tiles_per_block = tiles_per_block;
   p->col = col_idx;
   const int64_t steps = n_rows + nnz;
@@ -347,7 +349,8 @@ merbit_status merbit_plan_ex(const int32_t* row_ptr, const int32_t* col_idx, int
   const size_t nbb = sizeof(int32_t) * (size_t)(p->nb + 1);
   if (e == cudaSuccess) e = cudaMalloc(&p->tile_x, tb);
   if (e == cudaSuccess) e = cudaMalloc(&p->tile_y, tb);
-  if (e == cudaSuccess) e = cudaMalloc(&p->lane_desc, sizeof(uint32_t) * (size_t)std::max<int64_t>(p->lane_num, 1));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&p->lane_desc, (size_t)p->desc_bytes * (size_t)std::max<int64_t>(p->lane_num, 1));
   if (e == cudaSuccess) e = cudaMalloc(&p->bnd_row, nbb);
   if (e == cudaSuccess) e = cudaMalloc(&p->bnd_slot, nbb);
   if (e == cudaSuccess) e = cudaMalloc(&p->bnd_acc, sizeof(double) * (size_t)(p->nb + 1));
@@ -396,6 +399,7 @@ merbit_status merbit_plan_get_info(merbit_plan_t p, merbit_plan_info* info) {
   info->tile_y = p->tile_y;
   info->lane_desc = p->lane_desc;
   info->block_row = p->bnd_row;
+  info->desc_bytes = p->desc_bytes;
   return MERBIT_OK;
 }
 
@@ -407,7 +411,8 @@ merbit_status merbit_plan_export(merbit_plan_t p, uint32_t* tile_x, uint32_t* ti
   if (tile_x) MB_TRY(cudaMemcpy(tile_x, p->tile_x, tb, cudaMemcpyDeviceToHost));
   if (tile_y) MB_TRY(cudaMemcpy(tile_y, p->tile_y, tb, cudaMemcpyDeviceToHost));
   if (lane_desc && p->lane_num)
-    MB_TRY(cudaMemcpy(lane_desc, p->lane_desc, sizeof(uint32_t) * (size_t)p->lane_num, cudaMemcpyDeviceToHost));
+    MB_TRY(cudaMemcpy(lane_desc, p->lane_desc, (size_t)p->desc_bytes * (size_t)p->lane_num,
+                      cudaMemcpyDeviceToHost));
   if (block_row && p->nb)
     MB_TRY(cudaMemcpy(block_row, p->bnd_row, sizeof(int32_t) * (size_t)(p->nb + 1), cudaMemcpyDeviceToHost));
   else if (block_row)
@@ -484,8 +489,9 @@ merbit_status merbit_spmv(merbit_plan_t p, merbit_dtype dtype, const void* vals,
 merbit_status merbit_spmm(merbit_plan_t p, const float* vals, const float* X, float* Y, int64_t k,
                           int64_t ldx, int64_t ldy, void* stream) {
   if (merbit_status s = check_plan(p)) return s;
-  if (p->tiles_per_block != kTilesPerBlock)
-    return fail(MERBIT_EINVAL, "the SpMM needs a plan of %d tiles per block", kTilesPerBlock);
+  if (p->tiles_per_block != kTilesPerBlock || p->sigma > kSigmaMax)
+    return fail(MERBIT_EINVAL, "the SpMM needs a plan of %d tiles per block and sigma <= %d",
+                kTilesPerBlock, kSigmaMax);
   if (k < 0 || ldx < k || ldy < k) return fail(MERBIT_EINVAL, "need k >= 0, ldx >= k, ldy >= k");
   if (k == 0 || p->n_rows == 0) return MERBIT_OK;
   if (!Y || (p->nnz > 0 && (!vals || !X))) return fail(MERBIT_EINVAL, "vals, X or Y is NULL");
@@ -503,8 +509,9 @@ merbit_status merbit_ppr(merbit_plan_t p, const float* vals, const int32_t* seed
                          double* resid_out, double* resid_hist, void* stream) {
   if (merbit_status s = check_plan(p)) return s;
   if (p->n_rows != p->n_cols) return fail(MERBIT_EINVAL, "personalised PageRank needs a square plan");
-  if (p->tiles_per_block != kTilesPerBlock)
-    return fail(MERBIT_EINVAL, "personalised PageRank needs a plan of %d tiles per block", kTilesPerBlock);
+  if (p->tiles_per_block != kTilesPerBlock || p->sigma > kSigmaMax)
+    return fail(MERBIT_EINVAL, "personalised PageRank needs a plan of %d tiles per block and sigma <= %d",
+                kTilesPerBlock, kSigmaMax);
   if (!(alpha >= 0.0 && alpha < 1.0)) return fail(MERBIT_EINVAL, "alpha must be in [0, 1)");
   if (max_iter < 1) return fail(MERBIT_EINVAL, "max_iter must be >= 1");
   if (k < 1 || k > 1024) return fail(MERBIT_EINVAL, "k must be in [1, 1024]");

@@ -59,14 +59,14 @@ __global__ void __launch_bounds__(256)
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.lane_num; j += stride) {
     const int ti = (int)(j / kOmega);
-    const uint32_t d = __ldg(g.lane_desc + j);
-    int xk = (int)__ldg(g.tile_x + ti) + (int)(d & 511u);
-    int row = (int)(__ldg(g.tile_y + ti) & ~kMsb) + (int)((d >> 9) & 511u);
+    const LaneDesc d = decode_lane(g, load_desc(g, j));
+    int xk = (int)__ldg(g.tile_x + ti) + d.xo;
+    int row = (int)(__ldg(g.tile_y + ti) & ~kMsb) + d.yo;
     const int64_t left = (int64_t)g.steps - j * g.sigma;
     const int len = left < g.sigma ? (int)left : g.sigma;
     T gr = row < g.n_rows ? scale * gv[row] : T(0);
     for (int k = 0; k < len; ++k) {
-      if ((d >> (18 + k)) & 1u) {
+      if ((d.flags >> k) & 1u) {
         ++row;
         gr = row < g.n_rows ? scale * gv[row] : T(0);
       } else {

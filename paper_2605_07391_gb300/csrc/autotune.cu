@@ -93,7 +93,7 @@ merbit_status merbit_autotune(const int32_t* row_ptr, const int32_t* col_idx, in
     return afail(MERBIT_EINVAL, "need non-empty candidate lists and best");
   if (reps < 1) return afail(MERBIT_EINVAL, "reps must be >= 1");
   for (int i = 0; i < n_sigma; ++i)
-    if (sigmas[i] < 1 || sigmas[i] > kSigmaMax) return afail(MERBIT_EINVAL, "sigma candidate out of [1, 14]");
+    if (sigmas[i] < 1 || sigmas[i] > kSigmaMax64) return afail(MERBIT_EINVAL, "sigma candidate out of [1, 42]");
   for (int i = 0; i < n_block; ++i)
     if (blocks[i] != 4 && blocks[i] != 8 && blocks[i] != kMaxW)
       return afail(MERBIT_EINVAL, "tiles-per-block candidates must be 4, 8 or 16");

@@ -321,14 +321,14 @@ __global__ void batch_validate_kernel(const Geometry g, const int32_t* off, int 
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.lane_num; j += stride) {
     const int ti = (int)(j / kOmega);
-    const uint32_t d = __ldg(g.lane_desc + j);
-    int xk = (int)__ldg(g.tile_x + ti) + (int)(d & 511u);
-    int row = (int)(__ldg(g.tile_y + ti) & ~kMsb) + (int)((d >> 9) & 511u);
+    const LaneDesc d = decode_lane(g, load_desc(g, j));
+    int xk = (int)__ldg(g.tile_x + ti) + d.xo;
+    int row = (int)(__ldg(g.tile_y + ti) & ~kMsb) + d.yo;
     const int64_t left = (int64_t)g.steps - j * g.sigma;
     const int len = left < g.sigma ? (int)left : g.sigma;
     int gid = row < g.n_rows ? graph_of(off, G, row) : -1;
     for (int k = 0; k < len; ++k) {
-      if ((d >> (18 + k)) & 1u) {
+      if ((d.flags >> k) & 1u) {
         ++row;
         gid = row < g.n_rows ? graph_of(off, G, row) : -1;
       } else {
@@ -535,6 +535,7 @@ merbit_status merbit_batch_plan(const int32_t* row_ptr, const int32_t* col_idx, 
   if (!out) return bfail(MERBIT_EINVAL, "out is NULL");
   *out = nullptr;
   if (num_graphs < 1 || !graph_offsets) return bfail(MERBIT_EINVAL, "need num_graphs >= 1 and graph_offsets");
+  if (sigma > kSigmaMax) return bfail(MERBIT_EINVAL, "batches use 32-bit lane descriptors: sigma <= %d", kSigmaMax);
   if (graph_offsets[0] != 0 || graph_offsets[num_graphs] != n)
     return bfail(MERBIT_EINVAL, "graph_offsets must start at 0 and end at n");
   for (int g = 0; g < num_graphs; ++g)

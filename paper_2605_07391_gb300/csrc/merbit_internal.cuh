@@ -12,6 +12,7 @@ namespace merbit {
 
 constexpr int kOmega = 32;          // lanes per tile = warp size (Sec. 4.3)
 constexpr int kSigmaMax = 14;       // largest sigma of the 32-bit descriptor (Sec. 4.1.1)
+constexpr int kSigmaMax64 = 42;     // largest sigma of the 64-bit descriptor (11-bit offsets)
 constexpr int kTilesPerBlock = 8;   // W: tiles that share one shared-memory output buffer (default)
 constexpr int kThreads = kTilesPerBlock * kOmega;   // block kernels: 8 warps, one per tile of W = 8
 constexpr int kWarps = kThreads / 32;
@@ -42,6 +43,7 @@ struct Geometry {
   const int32_t* col_stage;   // column stream of the SpMV stages: col, or its hot-tagged copy
   const int32_t* hot_list;    // column of each hot-table slot
   int hot_n;                  // hot columns cached in shared memory by this launch (0: none)
+  int tag_cold;               // col_stage marks rarely used columns with bit 30 (gathered past L1)
   uint32_t wait_limit;        // polls of a stage wait before it gives up (drains use kSpinLimit)
   const int32_t* bnd_row;
   const int32_t* bnd_slot;
@@ -54,6 +56,7 @@ struct Geometry {
   int sigma;
   int W;           // tiles per block
   int stages;      // split kernel: stages in its ring (2 or 3)
+  int desc64;      // lane descriptors are 64-bit words (sigma > 14)
   int tile_num;
   int lane_num;
   int nb;          // number of blocks of tiles
@@ -66,6 +69,7 @@ struct merbit_plan_s {
   int num_sms = 0;
   int64_t n_rows = 0, n_cols = 0, nnz = 0;
   int sigma = 14, tiles_per_block = merbit::kTilesPerBlock;
+  int desc_bytes = 4;                    // 4: 32-bit lane descriptors; 8: 64-bit (sigma > 14)
   int spmv_kernel = 0;                   // MERBIT_KERNEL_AUTO / _CLASSIC / _SPLIT
   uint32_t wait_limit = merbit::kSpinLimit;   // polls of a stage wait (test hook lowers it)
   int64_t tile_num = 0, lane_num = 0, nb = 0;
@@ -76,6 +80,10 @@ struct merbit_plan_s {
   int32_t* hot_list = nullptr;
   int hot_n = 0;
   double hot_cover = 0.0;                // fraction of the nonzeros in hot columns
+  int hot_max = 0;                       // the table's settings, kept for a rebuild
+  double hot_min_cover = 0.0;
+  int cold_uses = 0;                     // columns used at most this often carry bit 30 in col_hot
+  double cold_cover = 0.0;               // fraction of the nonzeros in such columns
   uint32_t* tile_x = nullptr;
   uint32_t* tile_y = nullptr;
   uint32_t* lane_desc = nullptr;
@@ -102,16 +110,35 @@ struct merbit_plan_s {
     merbit::Geometry g;
     g.tile_x = tile_x; g.tile_y = tile_y; g.lane_desc = lane_desc; g.col = col;
     g.col_stage = col; g.hot_list = hot_list; g.hot_n = 0;   // a launch opts in to the table
+    g.tag_cold = 0;
     g.wait_limit = wait_limit;
     g.bnd_row = bnd_row; g.bnd_slot = bnd_slot;
     g.bnd_acc = bnd_acc; g.part = part; g.red = red;
     g.n_rows = (int)n_rows; g.nnz = (int)nnz; g.steps = (int)(nnz + n_rows);
-    g.sigma = sigma; g.W = tiles_per_block; g.stages = 3; g.tile_num = (int)tile_num; g.lane_num = (int)lane_num; g.nb = (int)nb;
+    g.sigma = sigma; g.W = tiles_per_block; g.stages = 3; g.desc64 = desc_bytes == 8;
+    g.tile_num = (int)tile_num; g.lane_num = (int)lane_num; g.nb = (int)nb;
     return g;
   }
 };
 
 namespace merbit {
+
+// A lane descriptor (Sec. 4.1.1): bit_flag << 2w | y_offset << w | x_offset, with w = 9 in
+// the 32-bit word (sigma <= 14) and w = 11 in the 64-bit word (sigma <= 42).
+struct LaneDesc {
+  int xo, yo;
+  uint64_t flags;   // bit k: step k of the lane is a down step
+};
+
+__device__ __forceinline__ uint64_t load_desc(const Geometry& g, int64_t j) {
+  return g.desc64 ? (uint64_t)__ldg(reinterpret_cast<const unsigned long long*>(g.lane_desc) + j)
+                  : (uint64_t)__ldg(g.lane_desc + j);
+}
+
+__device__ __forceinline__ LaneDesc decode_lane(const Geometry& g, uint64_t d) {
+  if (g.desc64) return LaneDesc{(int)(d & 2047u), (int)((d >> 11) & 2047u), d >> 22};
+  return LaneDesc{(int)(d & 511u), (int)((d >> 9) & 511u), d >> 18};
+}
 
 // ---- epilogue parameter blocks (device-side behaviour lives in spmv_kernel.cuh) ----
 

@@ -30,10 +30,13 @@ __device__ __forceinline__ int rows_before(const int32_t* __restrict__ row_ptr, 
 // One thread per lane j: start coordinate on diagonal j*sigma, sigma-step walk
 // into bit_flag, descriptor packing; lane 0 of each warp (= tile) writes the
 // tile start, with the MSB set when no lane of the tile takes a down step.
+// DT: the descriptor word (uint32_t: offsets of W_ = 9 bits, sigma <= 14; unsigned long long:
+// W_ = 11 bits, sigma <= 42).
+template <typename DT, int W_>
 __global__ void plan_tiles_kernel(const int32_t* __restrict__ row_ptr, int n_rows, int nnz,
                                   int sigma, int lane_num, int tile_num,
                                   uint32_t* __restrict__ tile_x, uint32_t* __restrict__ tile_y,
-                                  uint32_t* __restrict__ lane_desc) {
+                                  DT* __restrict__ lane_desc) {
   const int64_t j64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool active = j64 < lane_num;
@@ -52,17 +55,17 @@ __global__ void plan_tiles_kernel(const int32_t* __restrict__ row_ptr, int n_row
     const int len = min(sigma, steps - j * sigma);
     int x = cx, y = cy;
     int row_end = y < n_rows ? __ldg(row_ptr + y + 1) : nnz;
-    uint32_t flags = 0;
+    DT flags = 0;
     for (int k = 0; k < len; ++k) {
       if (x < row_end) {
         ++x;                       // right step: next nonzero of row y
       } else {
-        flags |= 1u << k;          // down step: row y is complete
+        flags |= DT(1) << k;       // down step: row y is complete
         ++y;
         row_end = y < n_rows ? __ldg(row_ptr + y + 1) : nnz;
       }
     }
-    lane_desc[j] = (flags << 18) | ((uint32_t)(cy - ty) << 9) | (uint32_t)(cx - tx);
+    lane_desc[j] = (flags << (2 * W_)) | ((DT)(cy - ty) << W_) | (DT)(cx - tx);
     end_y = y;
   }
   const bool single_row = __all_sync(0xffffffffu, end_y == ty);
@@ -125,9 +128,14 @@ cudaError_t build_tiles(const merbit_plan_s* p, const int32_t* row_ptr, cudaStre
   const int threads = 256;
   const int64_t total = p->lane_num + 1;
   const int blocks = (int)((total + threads - 1) / threads);
-  plan_tiles_kernel<<<blocks, threads, 0, st>>>(row_ptr, (int)p->n_rows, (int)p->nnz, p->sigma,
-                                                (int)p->lane_num, (int)p->tile_num, p->tile_x,
-                                                p->tile_y, p->lane_desc);
+  if (p->desc_bytes == 8)
+    plan_tiles_kernel<unsigned long long, 11><<<blocks, threads, 0, st>>>(
+        row_ptr, (int)p->n_rows, (int)p->nnz, p->sigma, (int)p->lane_num, (int)p->tile_num, p->tile_x,
+        p->tile_y, reinterpret_cast<unsigned long long*>(p->lane_desc));
+  else
+    plan_tiles_kernel<uint32_t, 9><<<blocks, threads, 0, st>>>(
+        row_ptr, (int)p->n_rows, (int)p->nnz, p->sigma, (int)p->lane_num, (int)p->tile_num, p->tile_x,
+        p->tile_y, p->lane_desc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nbt = (int)((p->nb + 1 + threads - 1) / threads);
@@ -180,15 +188,21 @@ int persistent_grid(const void* kernel, int threads, size_t smem, size_t smem_ma
   if (it != cache.end()) return it->second * num_sms;
   // the limit is raised once to the largest size any plan of this kernel needs, never lowered
   size_t& lim = attr[std::make_pair(dev, kernel)];
+  // a refused request (more shared memory than a CTA may have) is an answer, not an error
+  // for later calls: the runtime's last-error state is cleared
   if (smem_max > 48 * 1024 && lim < smem_max) {
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) !=
-        cudaSuccess)
+        cudaSuccess) {
+      cudaGetLastError();
       return 0;
+    }
     lim = smem_max;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
     return 0;
+  }
   cache[key] = per_sm;
   return per_sm * num_sms;
 }

@@ -42,9 +42,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       v[u] = XT(0);
       if (k < g.nnz) {
         const int c = (int)ld_stream(reinterpret_cast<const uint32_t*>(g.col_stage) + k, pol_stream);
-        const bool hot = c < 0;
-        if (hot) v[u] = tab[~c];
-        ld_x_if(v[u], x + c, !hot, pol_x);
+        v[u] = gather_x(g, c, x, tab, pol_x);
       }
     }
 #pragma unroll
@@ -83,7 +81,8 @@ cudaError_t launch_probe(const merbit_plan_s* p, const XT* x, XT* sink, cudaStre
   if (per_sm_total > 0) {
     const size_t need = (size_t)per_sm * (smem + (size_t)reserved + 1024);
     const int pct = (int)std::min<size_t>(100, (need * 100 + per_sm_total - 1) / (size_t)per_sm_total);
-    cudaFuncSetAttribute(kp, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    if (cudaFuncSetAttribute(kp, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
+      cudaGetLastError();   // a hint only
   }
   const int pgrid = persistent_grid(kp, kSplitThreads, smem, smem, p->num_sms);
   if (pgrid <= 0) return cudaErrorInvalidConfiguration;

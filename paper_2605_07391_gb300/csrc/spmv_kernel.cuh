@@ -140,6 +140,43 @@ __device__ __forceinline__ void ld_x_if(double& v, const double* p, bool pred, u
       : "l"(p), "r"((uint32_t)pred), "l"(pol));
 }
 
+// The same gather without an L1 allocation (for columns that are used too rarely to be
+// found in L1 again).
+__device__ __forceinline__ void ld_x_if_na(float& v, const float* p, bool pred, uint64_t pol) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+      "@q ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %3;\n\t}"
+      : "+f"(v)
+      : "l"(p), "r"((uint32_t)pred), "l"(pol));
+}
+
+__device__ __forceinline__ void ld_x_if_na(double& v, const double* p, bool pred, uint64_t pol) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+      "@q ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %3;\n\t}"
+      : "+d"(v)
+      : "l"(p), "r"((uint32_t)pred), "l"(pol));
+}
+
+// x[c] for a column c of the (possibly tagged) staged column stream: c < 0 names hot-table
+// slot ~c (shared memory); with tag_cold, bit 30 marks a rarely used column, gathered
+// without an L1 allocation.
+template <typename XT>
+__device__ __forceinline__ XT gather_x(const Geometry& g, int c, const XT* x, const XT* tab, uint64_t pol_x) {
+  const bool hot = c < 0;
+  XT v = XT(0);
+  if (hot) v = tab[~c];
+  if (g.tag_cold) {
+    const bool cold = (c >> 30) & 1;
+    const int cc = c & 0x3FFFFFFF;
+    ld_x_if(v, x + cc, !hot && !cold, pol_x);
+    ld_x_if_na(v, x + cc, !hot && cold, pol_x);
+  } else {
+    ld_x_if(v, x + c, !hot, pol_x);
+  }
+  return v;
+}
+
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t pol) {
   uint32_t v;
   asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
@@ -463,11 +500,7 @@ struct Stages {
   __device__ __forceinline__ void gather(int s, const StageInfo& in, int k, const XT* x, const XT* tab,
                                          uint64_t pol_x, AT& xv) const {
     const int c = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
-    const bool hot = c < 0;
-    XT v = XT(0);
-    if (hot) v = tab[~c];
-    ld_x_if(v, x + c, !hot, pol_x);
-    xv = static_cast<AT>(v);
+    xv = static_cast<AT>(gather_x(g, c, x, tab, pol_x));
   }
   // the value of nonzero k (1 for a pattern): staged, or read from global memory
   __device__ __forceinline__ AT value(int s, const StageInfo& in, int k) const {
@@ -513,13 +546,25 @@ struct BlockOrder {
   }
 };
 
+// A lane descriptor, streamed once per launch (L2 evict_first).
+__device__ __forceinline__ uint64_t ld_desc(const Geometry& g, int j, uint64_t pol) {
+  if (g.desc64) {
+    unsigned long long v;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;"
+                 : "=l"(v)
+                 : "l"(reinterpret_cast<const unsigned long long*>(g.lane_desc) + j), "l"(pol));
+    return v;
+  }
+  return ld_stream(g.lane_desc + j, pol);
+}
+
 // One warp reduces one tile of a staged block into the block's row sums (Algorithm
 // tile_normal_tackle with WarpSegmentedSum; tile_fast_tackle for a tile marked as part
 // of a single row).  pt: the tile's first product; sy: the row sums from the tile's first
 // row y_ws on; desc: this lane's descriptor; j: this lane's global lane index.
 template <typename AT>
 __device__ __forceinline__ void reduce_tile(const Geometry& g, const AT* pt, AT* sy, uint32_t txs,
-                                            uint32_t txe, uint32_t tys, int y_ws, uint32_t desc,
+                                            uint32_t txe, uint32_t tys, int y_ws, uint64_t desc,
                                             int j, int lane) {
   if (tys & kMsb) {
     // single-row tile: plain warp reduction, no descriptor
@@ -527,19 +572,25 @@ __device__ __forceinline__ void reduce_tile(const Geometry& g, const AT* pt, AT*
     for (int k = lane; k < (int)(txe - txs); k += 32) sum += pt[k];
     sum = warp_sum(sum);
     if (lane == 0) atomicAdd(sy, sum);
-  } else {
-    const bool active = j < g.lane_num;
-    const int lane_len = active ? min(g.sigma, g.steps - j * g.sigma) : 0;
+    return;
+  }
+  const bool active = j < g.lane_num;
+  const int lane_len = active ? min(g.sigma, g.steps - j * g.sigma) : 0;
+  AT sum = AT(0);
+  int yo;
+  bool head;
+  if (!g.desc64) {
+    // 32-bit descriptor (sigma <= 14): the steps unrolled, each product addressed from
+    // the descriptor alone (step k consumes product k - (down steps before k)), so no
+    // load waits on the running sum
+    const uint32_t d = (uint32_t)desc;
     const uint32_t valid = (1u << lane_len) - 1u;
-    const uint32_t dm = (desc >> 18) & valid;     // down steps
-    const uint32_t rm = ~(desc >> 18) & valid;    // right steps
-    const int y0 = active ? (int)((desc >> 9) & 511u) : (g.n_rows - y_ws);
-    const AT* pl = pt + (int)(desc & 511u);       // this lane's first product
-    AT sum = AT(0);
+    const uint32_t dm = (d >> 18) & valid;     // down steps
+    const uint32_t rm = ~(d >> 18) & valid;    // right steps
+    const int y0 = active ? (int)((d >> 9) & 511u) : (g.n_rows - y_ws);
+    const AT* pl = pt + (int)(d & 511u);       // this lane's first product
 #pragma unroll
     for (int k = 0; k < kSigmaMax; ++k) {
-      // step k consumes product k - (down steps before k), an address that follows
-      // from the descriptor alone
       const int nd = __popc(dm & ((1u << k) - 1u));
       const AT pv = pl[k - nd];
       if ((dm >> k) & 1u) {
@@ -552,28 +603,47 @@ __device__ __forceinline__ void reduce_tile(const Geometry& g, const AT* pt, AT*
         sum += pv;
       }
     }
-    const int yo = y0 + __popc(dm);
-    const bool head = lane == 0 || dm != 0u;
-    // segmented inclusive scan of trailing sums; heads start segments
-    AT sv_ = sum;
-    int f = head ? 1 : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      if (__all_sync(0xffffffffu, f)) break;
-      const AT up = __shfl_up_sync(0xffffffffu, sv_, o);
-      const int fu = __shfl_up_sync(0xffffffffu, f, o);
-      if (lane >= o && !f) {
-        sv_ += up;
-        f = fu;
+    yo = y0 + __popc(dm);
+    head = lane == 0 || dm != 0u;
+  } else {
+    // 64-bit descriptor (sigma 15..42): the same walk as a loop over the lane's steps
+    const uint64_t valid = lane_len >= 64 ? ~0ull : ((1ull << lane_len) - 1ull);
+    const uint64_t dm = (desc >> 22) & valid;
+    const int y0 = active ? (int)((desc >> 11) & 2047u) : (g.n_rows - y_ws);
+    const AT* pl = pt + (int)(desc & 2047u);
+    int nd = 0;
+    for (int k = 0; k < lane_len; ++k) {
+      if ((dm >> k) & 1ull) {
+        if (nd == 0) atomicAdd(sy + y0, sum);
+        else sy[y0 + nd] = sum;
+        sum = AT(0);
+        ++nd;
+      } else {
+        sum += pl[k - nd];
       }
     }
-    // a head lane adds the segment that ends just before it; lane 0 takes
-    // the tile's final segment (ending at lane 31)
-    const int src = lane == 0 ? 31 : lane - 1;
-    const AT seg = __shfl_sync(0xffffffffu, sv_, src);
-    const int row = __shfl_sync(0xffffffffu, yo, src);
-    if (head) atomicAdd(sy + row, seg);
+    yo = y0 + nd;
+    head = lane == 0 || dm != 0ull;
   }
+  // segmented inclusive scan of trailing sums; heads start segments
+  AT sv_ = sum;
+  int f = head ? 1 : 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    if (__all_sync(0xffffffffu, f)) break;
+    const AT up = __shfl_up_sync(0xffffffffu, sv_, o);
+    const int fu = __shfl_up_sync(0xffffffffu, f, o);
+    if (lane >= o && !f) {
+      sv_ += up;
+      f = fu;
+    }
+  }
+  // a head lane adds the segment that ends just before it; lane 0 takes
+  // the tile's final segment (ending at lane 31)
+  const int src = lane == 0 ? 31 : lane - 1;
+  const AT seg = __shfl_sync(0xffffffffu, sv_, src);
+  const int row = __shfl_sync(0xffffffffu, yo, src);
+  if (head) atomicAdd(sy + row, seg);
 }
 
 template <typename VT, typename XT, typename AT, typename Epi>
@@ -624,7 +694,8 @@ __global__ void __launch_bounds__(kThreads, 3)
 
     // tile metadata of this warp's tiles (warp, warp + 8 while < W), loaded before the
     // wait to hide latency
-    uint32_t txs[kMaxTpw], txe[kMaxTpw], tys[kMaxTpw], desc[kMaxTpw];
+    uint32_t txs[kMaxTpw], txe[kMaxTpw], tys[kMaxTpw];
+    uint64_t desc[kMaxTpw];
 #pragma unroll
     for (int t = 0; t < kMaxTpw; ++t) {
       const int wt = warp + t * kWarps;
@@ -635,7 +706,7 @@ __global__ void __launch_bounds__(kThreads, 3)
         txs[t] = __ldg(g.tile_x + ti);
         txe[t] = __ldg(g.tile_x + ti + 1);
         tys[t] = __ldg(g.tile_y + ti);
-        if (!(tys[t] & kMsb) && j < g.lane_num) desc[t] = ld_stream(g.lane_desc + j, pol_stream);
+        if (!(tys[t] & kMsb) && j < g.lane_num) desc[t] = ld_desc(g, j, pol_stream);
       }
     }
     // geometry for the copy issued at the end of this iteration
@@ -861,7 +932,8 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       const int v = blk(kb);
       const int s = i % S;
       constexpr int CW = kSplitConsumers / 32, TPW = kMaxTpw;
-      uint32_t txs[TPW], txe[TPW], tys[TPW], desc[TPW];
+      uint32_t txs[TPW], txe[TPW], tys[TPW];
+      uint64_t desc[TPW];
 #pragma unroll
       for (int t = 0; t < TPW; ++t) {
         const int ti = v * g.W + warp + t * CW;
@@ -871,7 +943,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
           txs[t] = __ldg(g.tile_x + ti);
           txe[t] = __ldg(g.tile_x + ti + 1);
           tys[t] = __ldg(g.tile_y + ti);
-          if (!(tys[t] & kMsb) && j < g.lane_num) desc[t] = ld_stream(g.lane_desc + j, pol_stream);
+          if (!(tys[t] & kMsb) && j < g.lane_num) desc[t] = ld_desc(g, j, pol_stream);
         }
       }
       BlockSpan next{0, 0, 0u, 0u};
@@ -1017,12 +1089,13 @@ __global__ void __launch_bounds__(256) merbit_finalize_kernel(const Geometry g, 
 template <typename XT>
 inline size_t add_hot_table(const merbit_plan_s* p, Geometry& g, const void* kern, size_t stages,
                             int per_sm) {
-  if (p->hot_n <= 0 || !p->col_hot || per_sm <= 0) return stages;
+  if (!p->col_hot || per_sm <= 0) return stages;
   const size_t need = stages + ((sizeof(XT) * (size_t)p->hot_n + 15) & ~size_t(15));
-  if (need > smem_room(kern, per_sm)) return stages;
+  if (p->hot_n > 0 && need > smem_room(kern, per_sm)) return stages;
   g.col_stage = p->col_hot;
   g.hot_list = p->hot_list;
   g.hot_n = p->hot_n;
+  g.tag_cold = p->cold_uses > 0;
   return need;
 }
 
@@ -1059,12 +1132,15 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   // column-only stages need 4-byte products (they are written over the column indices)
   constexpr bool kColsOk = sizeof(AT) == 4 && !IsUnit<VT>::value;
   const int kind = p->spmv_kernel;
+  // A split kernel that was asked for but cannot hold even one CTA's stages on an SM (large
+  // sigma x block size with 8-byte values) gives way to the classic kernel, whose ring
+  // has two stages.
   if constexpr (kColsOk) {
     if (kind == MERBIT_KERNEL_SPLIT_COLS) {
       size_t smem = 0;
       split = split_config<VT, XT, AT, Epi, false>(p, g, grid, smem, true);
-      if (!split) return cudaErrorInvalidConfiguration;
-      merbit_spmv_split_kernel<VT, XT, AT, Epi, false><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
+      if (split)
+        merbit_spmv_split_kernel<VT, XT, AT, Epi, false><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
     }
   }
   if (split) {
@@ -1072,9 +1148,8 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   } else if (kind == MERBIT_KERNEL_SPLIT || kind == MERBIT_KERNEL_SPLIT_COLS || kind == MERBIT_KERNEL_SPLIT2 ||
              (kind == MERBIT_KERNEL_AUTO && sizeof(VT) >= 4)) {
     size_t smem = 0;
-    const bool forced = kind != MERBIT_KERNEL_AUTO;
-    split = split_config<VT, XT, AT, Epi, true>(p, g, grid, smem, forced);
-    if (!split && forced) return cudaErrorInvalidConfiguration;
+    g = p->geom();
+    split = split_config<VT, XT, AT, Epi, true>(p, g, grid, smem, kind != MERBIT_KERNEL_AUTO);
     if (split) merbit_spmv_split_kernel<VT, XT, AT, Epi, true><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
   }
   if (!split) {

@@ -33,7 +33,7 @@ EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_
            "merbit_spmv_noalloc_status",
            "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
            "merbit_plan_set_hot_columns", "merbit_gather_probe", "merbit_plan_set_wait_limit",
-           "merbit_autotune", "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
+           "merbit_autotune", "merbit_plan_set_cold_columns", "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
            "merbit_batch_get_plan", "merbit_batch_destroy", "merbit_autotune_sigma", "merbit_bicgstab",
            "merbit_last_error",
            "merbit_version"]
@@ -51,7 +51,8 @@ class PlanInfo(ctypes.Structure):
                 ("tiles_per_block", ctypes.c_int32), ("tile_num", ctypes.c_int64),
                 ("lane_num", ctypes.c_int64), ("block_num", ctypes.c_int64),
                 ("tile_x", ctypes.c_void_p), ("tile_y", ctypes.c_void_p),
-                ("lane_desc", ctypes.c_void_p), ("block_row", ctypes.c_void_p)]
+                ("lane_desc", ctypes.c_void_p), ("block_row", ctypes.c_void_p),
+                ("desc_bytes", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -82,6 +83,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_plan_set_kernel": [vp, ctypes.c_int],
             "merbit_gather_probe": [vp, i32, vp, vp, vp],
             "merbit_plan_set_wait_limit": [vp, i32],
+            "merbit_plan_set_cold_columns": [vp, i32, vp, ctypes.POINTER(dbl)],
             "merbit_plan_set_hot_columns": [vp, i32, dbl, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)],
             "merbit_plan_export": [vp, vp, vp, vp, vp],
             "merbit_spmv": [vp, i32, vp, vp, vp],
@@ -212,7 +214,8 @@ class Plan:
         """Host copies of the TILE arrays and block rows (merbit_plan_export)."""
         inf = self.info()
         t = TileArrays(np.empty(inf.tile_num + 1, np.uint32), np.empty(inf.tile_num + 1, np.uint32),
-                       np.empty(inf.lane_num, np.uint32), np.empty(inf.block_num + 1, np.int32))
+                       np.empty(inf.lane_num, np.uint64 if inf.desc_bytes == 8 else np.uint32),
+                       np.empty(inf.block_num + 1, np.int32))
         _check("merbit_plan_export", load().merbit_plan_export(
             self.handle, *(ctypes.c_void_p(a.ctypes.data) for a in
                            (t.tile_x, t.tile_y, t.lane_desc, t.block_row))))
@@ -221,6 +224,14 @@ class Plan:
     def set_kernel(self, kernel: str):
         """Block kernel for later products: "auto", "classic" or "split"."""
         _check("merbit_plan_set_kernel", load().merbit_plan_set_kernel(self.handle, KERNELS[kernel]))
+
+    def set_cold_columns(self, max_uses: int, stream=None) -> float:
+        """merbit_plan_set_cold_columns: gather columns used at most max_uses times past L1
+        (0 clears).  Returns the fraction of the nonzeros in such columns."""
+        cov = ctypes.c_double(0.0)
+        _check("merbit_plan_set_cold_columns", load().merbit_plan_set_cold_columns(
+            self.handle, int(max_uses), _stream(stream), ctypes.byref(cov)))
+        return cov.value
 
     def set_wait_limit(self, polls: int):
         """merbit_plan_set_wait_limit (test aid): polls of a stage wait before it gives up;

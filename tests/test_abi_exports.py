@@ -43,7 +43,7 @@ def test_errors_without_device_work():
     assert st == 1 and b"row_ptr" in lib.merbit_last_error()
     st = lib.merbit_plan_ex(ctypes.c_void_p(16), None, -1, 10, 0, 14, 8, None, ctypes.byref(h))
     assert st == 1
-    st = lib.merbit_plan_ex(ctypes.c_void_p(16), ctypes.c_void_p(16), 10, 10, 5, 15, 8, None,
+    st = lib.merbit_plan_ex(ctypes.c_void_p(16), ctypes.c_void_p(16), 10, 10, 5, 43, 8, None,
                             ctypes.byref(h))
     assert st == 1 and b"sigma" in lib.merbit_last_error()
     st = lib.merbit_plan_ex(ctypes.c_void_p(16), ctypes.c_void_p(16), 2**30, 2**30, 2**30, 14, 8,

@@ -118,3 +118,66 @@ def test_autotune_searches_sigma_block_kernel_table(cuda_device, dtype):
     y = mb.spmv(p, vals, x)
     y_ref, d = oracle.spmv(a.row_ptr, a.col, as_f64(vals), as_f64(x))
     check_rel(as_f64(y), y_ref, d, 1e-12 if dtype == torch.float64 else 1e-5, f"autotuned {best}")
+
+
+# ---------------------------------------------------------------- 64-bit lane descriptors
+
+@pytest.mark.parametrize("sigma", [15, 21, 28, 42])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_plan_64bit_descriptors_bit_exact(cuda_device, case, sigma):
+    a = CASES[case]()
+    p, _ = _plan(a, sigma, 8)
+    assert p.info().desc_bytes == 8
+    t = p.tiles()
+    ref = oracle.build_tile(a.row_ptr, sigma)
+    assert ref["lane_desc"].dtype == np.uint64
+    assert np.array_equal(t.tile_x, ref["tile_x"]) and np.array_equal(t.tile_y, ref["tile_y"])
+    assert np.array_equal(t.lane_desc, ref["lane_desc"])
+    assert np.array_equal(t.block_row.astype(np.int64), oracle.block_boundary_rows(ref["tile_y"], ref["tile_num"], 8))
+
+
+@pytest.mark.parametrize("kernel", ["classic", "split", "split_cols"])
+@pytest.mark.parametrize("W", [4, 8])
+@pytest.mark.parametrize("sigma", [17, 28, 42])
+def test_spmv_64bit_descriptors(cuda_device, sigma, W, kernel):
+    for case in ("rmat15_hubs", "ragged"):
+        a = CASES[case]()
+        p, _ = _plan(a, sigma, W, kernel)
+        for dtype in (torch.float32, torch.float64):
+            vals = torch.from_numpy(a.val).to("cuda", dtype)
+            x = torch.from_numpy(inputs.uniform_vector(a.n_cols, 7)).to("cuda", dtype)
+            y = torch.full((a.n_rows,), float("nan"), dtype=dtype, device="cuda")
+            for _ in range(2):
+                mb.spmv(p, vals, x, y)
+            p.sync()
+            y_ref, d = oracle.spmv(a.row_ptr, a.col, as_f64(vals), as_f64(x))
+            check_rel(as_f64(y), y_ref, d, TOL[dtype], f"{case} sigma={sigma} W={W} {kernel} {dtype}")
+        p.destroy()
+
+
+def test_pagerank_and_gradient_on_64bit_plan(cuda_device):
+    a = inputs.rmat_transition(14, 16, 1)
+    p, _ = _plan(a, 28, 4)
+    v64 = torch.from_numpy(a.val).cuda()
+    pi, info = mb.pagerank(p, v64, ALPHA, tol=1e-10, mode="ir_bf16", inner_sweeps=12, max_iter=40)
+    assert info["converged"]
+    assert oracle.pagerank_residual(a.row_ptr, a.col, a.val, as_f64(pi), ALPHA) < 1.1e-10
+    # per-nonzero products g[row] x[col] walk the 64-bit descriptors
+    g = torch.from_numpy(inputs.uniform_vector(a.n_rows, 3)).cuda()
+    x = torch.from_numpy(inputs.uniform_vector(a.n_cols, 4)).cuda()
+    out = mb.sddmm(p, g, x, 1.0)
+    np.testing.assert_array_equal(as_f64(out), oracle.sddmm(a.row_ptr, a.col, as_f64(g), as_f64(x)))
+
+
+def test_64bit_plans_rejected_where_unsupported(cuda_device):
+    a = inputs.rmat_transition(12, 8, 1)
+    rp = torch.from_numpy(a.row_ptr).cuda()
+    col = torch.from_numpy(a.col).cuda()
+    p = mb.plan(rp, col, sigma=20)
+    vals = torch.from_numpy(a.val).cuda().float()
+    with pytest.raises(mb.MerbitError):
+        mb.spmm(p, vals, torch.ones(a.n_cols, 4, device="cuda"))
+    with pytest.raises(mb.MerbitError):
+        mb.Batch(rp, col, np.array([0, a.n_rows]), sigma=20)
+    with pytest.raises(mb.MerbitError):
+        mb.plan(rp, col, sigma=43)
