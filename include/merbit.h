@@ -130,11 +130,6 @@ merbit_status merbit_plan_export(merbit_plan_t plan, uint32_t* tile_x, uint32_t*
  *   MERBIT_KERNEL_SPLIT: 512 threads per CTA; 256 producer threads gather x and form
  *     the products of the next blocks while the 256 consumer threads reduce and
  *     commit the current one (three stages), so gathers and scans overlap.
- *   MERBIT_KERNEL_SPLIT_COLS: the split kernel with stages of column indices only;
- *     the producers read each value from global memory (coalesced, streamed past L1)
- *     beside its gather and write the products over the column indices, which halves
- *     the stages' shared memory and leaves L1 more room for x.  For values whose
- *     products are 4 bytes wide (f32, bf16, f16); other value types use SPLIT.
  *   MERBIT_KERNEL_SPLIT2: the split kernel with a ring of two stages instead of three
  *     (less shared memory, so more L1 for x; the copy of block i + 2 then overlaps only
  *     the producers' work on block i + 1).
@@ -147,8 +142,7 @@ enum {
   MERBIT_KERNEL_AUTO = 0,
   MERBIT_KERNEL_CLASSIC = 1,
   MERBIT_KERNEL_SPLIT = 2,
-  MERBIT_KERNEL_SPLIT_COLS = 3,
-  MERBIT_KERNEL_SPLIT2 = 4
+  MERBIT_KERNEL_SPLIT2 = 3
 };
 
 /* Choose the block kernel for every later call on this plan (host-side setting,
@@ -173,20 +167,6 @@ merbit_status merbit_plan_set_kernel(merbit_plan_t plan, int kernel);
  */
 merbit_status merbit_plan_set_hot_columns(merbit_plan_t plan, int max_hot, double min_cover,
                                           void* stream, int* hot_n_out, double* cover_out);
-
-/*
- * merbit_plan_set_cold_columns — mark the columns referenced by at most max_uses nonzeros
- * (0 clears the marks) in the plan's tagged copy of col_idx (the copy of
- * merbit_plan_set_hot_columns, rebuilt here with the plan's current table settings): the
- * products gather x at those columns without allocating them in L1, so the lines of x
- * that are used again stay there.  No counterpart in the paper (a GB300 choice for the x
- * gather of Sec. 4.2).  Only for n_cols <= 2^30 (bit 30 of a column index carries the
- * mark); otherwise nothing is marked.  Products are unchanged.  *cover_out (host, may be
- * NULL) = the fraction of the nonzeros in marked columns.  Synchronises `stream`.
- * Errors: EINVAL, ENOMEM, ECUDA.
- */
-merbit_status merbit_plan_set_cold_columns(merbit_plan_t plan, int max_uses, void* stream,
-                                           double* cover_out);
 
 /*
  * merbit_gather_probe — a measurement aid with no counterpart in the paper: one pass of

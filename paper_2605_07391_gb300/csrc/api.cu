@@ -423,7 +423,7 @@ merbit_status merbit_plan_export(merbit_plan_t p, uint32_t* tile_x, uint32_t* ti
 merbit_status merbit_plan_set_kernel(merbit_plan_t p, int kernel) {
   if (merbit_status s = check_plan(p)) return s;
   if (kernel < MERBIT_KERNEL_AUTO || kernel > MERBIT_KERNEL_SPLIT2)
-    return fail(MERBIT_EINVAL, "kernel must be MERBIT_KERNEL_AUTO, _CLASSIC, _SPLIT, _SPLIT_COLS or _SPLIT2");
+    return fail(MERBIT_EINVAL, "kernel must be MERBIT_KERNEL_AUTO, _CLASSIC, _SPLIT or _SPLIT2");
   p->spmv_kernel = kernel;
   return MERBIT_OK;
 }
@@ -475,6 +475,10 @@ merbit_status merbit_spmv_ex(merbit_plan_t p, merbit_dtype vdt, merbit_dtype xdt
                 "unsupported (vals, x/y) dtypes: (F32,F32), (F64,F64), (BF16,F32), (F16,F32); "
                 "scale_exp only with 16-bit values");
   }
+  if (e == cudaErrorInvalidConfiguration)
+    return fail(MERBIT_EINVAL, "spmv launch: a block of this plan (sigma %d x %d tiles) needs more "
+                "shared memory than one CTA may use for these value types; use a smaller sigma or "
+                "tiles_per_block", p->sigma, p->tiles_per_block);
   if (e != cudaSuccess) return cuda_fail(e, "spmv launch");
   return MERBIT_OK;
 }

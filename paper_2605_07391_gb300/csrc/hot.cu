@@ -7,10 +7,8 @@
 // use, and streams a copy of the column array in which each of them is
 // replaced by ~slot (a negative index).  Every launch of the SpMV then copies
 // x at those columns into shared memory once per CTA and takes the gathers of
-// tagged nonzeros from there (see spmv_kernel.cuh).  The same copy can also
-// mark, with bit 30, the columns used only a few times: their gathers skip the
-// L1 allocation, so they do not evict the lines of x that are used again.  No
-// counterpart in the paper: these are GB300 choices for the x gather of Sec. 4.2.
+// tagged nonzeros from there (see spmv_kernel.cuh).  No counterpart in the
+// paper: this is a GB300 choice for the x gather of Sec. 4.2.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
@@ -75,30 +73,14 @@ __global__ void mark_slots_kernel(const int32_t* __restrict__ hot_list, int h,
   if (s < h) slot_of[hot_list[s]] = (uint32_t)(~s);
 }
 
-// out[k] = ~slot for a hot column, else the column with bit 30 set when it is used at most
-// cold_uses times (slot_of holds ~slot for hot columns and the use count otherwise)
 __global__ void tag_columns_kernel(const int32_t* __restrict__ col, int64_t nnz,
-                                   const uint32_t* __restrict__ slot_of, uint32_t cold_uses,
-                                   int32_t* __restrict__ out) {
+                                   const uint32_t* __restrict__ slot_of, int32_t* __restrict__ out) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = __ldg(col + k);
     const int32_t t = (int32_t)__ldg(slot_of + c);
-    out[k] = t < 0 ? t : ((uint32_t)t <= cold_uses ? (c | 0x40000000) : c);
+    out[k] = t < 0 ? t : c;
   }
-}
-
-// the number of nonzeros whose column is used at most cold_uses times
-__global__ void count_cold_kernel(const uint32_t* __restrict__ cnt, int64_t n, uint32_t cold_uses,
-                                  unsigned long long* __restrict__ total) {
-  unsigned long long s = 0;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t v = cnt[c];
-    if ((int32_t)v >= 0 && v <= cold_uses) s += v;
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
 }
 
 void drop_table(merbit_plan_s* p) {
@@ -108,7 +90,6 @@ void drop_table(merbit_plan_s* p) {
   p->hot_list = nullptr;
   p->hot_n = 0;
   p->hot_cover = 0.0;
-  p->cold_cover = 0.0;
 }
 
 merbit_status fail_hot(merbit_status s, const char* what, cudaError_t e) {
@@ -126,11 +107,7 @@ namespace merbit {
 // its columns hold at least min_cover of the nonzeros.
 merbit_status build_hot_table(merbit_plan_s* p, int max_hot, double min_cover, cudaStream_t st) {
   drop_table(p);
-  p->hot_max = max_hot;
-  p->hot_min_cover = min_cover;
-  // bit 30 can tag a column only while every column index is below 2^30
-  const uint32_t cold = p->n_cols <= (int64_t(1) << 30) && p->cold_uses > 0 ? (uint32_t)p->cold_uses : 0u;
-  if ((max_hot <= 0 && cold == 0) || p->nnz == 0 || p->n_cols == 0) return MERBIT_OK;
+  if (max_hot <= 0 || p->nnz == 0 || p->n_cols == 0) return MERBIT_OK;
   const int64_t n = p->n_cols, nnz = p->nnz;
   uint32_t* cnt = nullptr;
   uint32_t* hist = nullptr;
@@ -146,8 +123,8 @@ merbit_status build_hot_table(merbit_plan_s* p, int max_hot, double min_cover, c
   };
   cudaError_t e = cudaMalloc(&cnt, sizeof(uint32_t) * (size_t)n);
   if (e == cudaSuccess) e = cudaMalloc(&hist, sizeof(uint32_t) * kHistBins);
-  if (e == cudaSuccess) e = cudaMalloc(&sel_col, sizeof(int32_t) * (size_t)std::max(max_hot, 1));
-  if (e == cudaSuccess) e = cudaMalloc(&sel_cnt, sizeof(uint32_t) * (size_t)std::max(max_hot, 2));
+  if (e == cudaSuccess) e = cudaMalloc(&sel_col, sizeof(int32_t) * (size_t)max_hot);
+  if (e == cudaSuccess) e = cudaMalloc(&sel_cnt, sizeof(uint32_t) * (size_t)max_hot);
   if (e == cudaSuccess) e = cudaMalloc(&nsel, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kHistBins, st);
@@ -175,20 +152,16 @@ merbit_status build_hot_table(merbit_plan_s* p, int max_hot, double min_cover, c
     --thr;
     above += h[thr];
   }
-  if (max_hot <= 0) above = 0;
-  if (above == 0 && cold == 0) {
+  if (above == 0) {
     cleanup();
     return MERBIT_OK;
   }
+  select_kernel<<<grid, 256, 0, st>>>(cnt, n, (uint32_t)thr, max_hot, sel_col, sel_cnt, nsel);
   int ns = 0;
-  e = cudaSuccess;
-  if (above > 0) {
-    select_kernel<<<grid, 256, 0, st>>>(cnt, n, (uint32_t)thr, max_hot, sel_col, sel_cnt, nsel);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, nsel, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    ns = std::min(ns, max_hot);
-  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, nsel, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  ns = std::min(ns, max_hot);
   std::vector<int32_t> hc((size_t)ns);
   std::vector<uint32_t> hn((size_t)ns);
   if (e == cudaSuccess && ns)
@@ -212,33 +185,18 @@ merbit_status build_hot_table(merbit_plan_s* p, int max_hot, double min_cover, c
     list[(size_t)i] = hc[(size_t)order[(size_t)i]];
     covered += hn[(size_t)order[(size_t)i]];
   }
-  double cover = covered / (double)nnz;
-  if (cover < min_cover) {   // the table is not worth its shared memory
-    ns = 0;
-    cover = 0.0;
-  }
-  if (ns == 0 && cold == 0) {
+  const double cover = covered / (double)nnz;
+  if (ns == 0 || cover < min_cover) {
     cleanup();
     return MERBIT_OK;
   }
-  unsigned long long cold_nnz = 0;
-  if (ns > 0) e = cudaMalloc(&p->hot_list, sizeof(int32_t) * (size_t)ns);
+  e = cudaMalloc(&p->hot_list, sizeof(int32_t) * (size_t)ns);
   if (e == cudaSuccess) e = cudaMalloc(&p->col_hot, sizeof(int32_t) * (size_t)nnz);
-  if (e == cudaSuccess && ns > 0)
+  if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->hot_list, list.data(), sizeof(int32_t) * (size_t)ns, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && cold > 0) {
-    // reuse the selection counter as the cold total (zeroed first)
-    e = cudaMemsetAsync(sel_cnt, 0, sizeof(unsigned long long), st);
-    if (e == cudaSuccess) {
-      count_cold_kernel<<<grid, 256, 0, st>>>(cnt, n, cold, reinterpret_cast<unsigned long long*>(sel_cnt));
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&cold_nnz, sel_cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-  }
   if (e == cudaSuccess) {
-    if (ns > 0) mark_slots_kernel<<<(ns + 255) / 256, 256, 0, st>>>(p->hot_list, ns, cnt);
-    tag_columns_kernel<<<grid, 256, 0, st>>>(p->col, nnz, cnt, cold, p->col_hot);
+    mark_slots_kernel<<<(ns + 255) / 256, 256, 0, st>>>(p->hot_list, ns, cnt);
+    tag_columns_kernel<<<grid, 256, 0, st>>>(p->col, nnz, cnt, p->col_hot);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -250,7 +208,6 @@ merbit_status build_hot_table(merbit_plan_s* p, int max_hot, double min_cover, c
   }
   p->hot_n = ns;
   p->hot_cover = cover;
-  p->cold_cover = (double)cold_nnz / (double)nnz;
   return MERBIT_OK;
 }
 
@@ -274,23 +231,6 @@ merbit_status merbit_plan_set_hot_columns(merbit_plan_t p, int max_hot, double m
   const merbit_status s = build_hot_table(p, max_hot, min_cover, static_cast<cudaStream_t>(stream));
   if (hot_n_out) *hot_n_out = p->hot_n;
   if (cover_out) *cover_out = p->hot_cover;
-  return s;
-}
-
-merbit_status merbit_plan_set_cold_columns(merbit_plan_t p, int max_uses, void* stream,
-                                           double* cover_out) {
-  set_last_error("");
-  if (!p) {
-    set_last_error("plan is NULL");
-    return MERBIT_EINVAL;
-  }
-  if (max_uses < 0) {
-    set_last_error("max_uses must be >= 0");
-    return MERBIT_EINVAL;
-  }
-  p->cold_uses = max_uses;
-  const merbit_status s = build_hot_table(p, p->hot_max, p->hot_min_cover, static_cast<cudaStream_t>(stream));
-  if (cover_out) *cover_out = p->cold_cover;
   return s;
 }
 

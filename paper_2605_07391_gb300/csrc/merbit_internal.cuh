@@ -43,7 +43,6 @@ struct Geometry {
   const int32_t* col_stage;   // column stream of the SpMV stages: col, or its hot-tagged copy
   const int32_t* hot_list;    // column of each hot-table slot
   int hot_n;                  // hot columns cached in shared memory by this launch (0: none)
-  int tag_cold;               // col_stage marks rarely used columns with bit 30 (gathered past L1)
   uint32_t wait_limit;        // polls of a stage wait before it gives up (drains use kSpinLimit)
   const int32_t* bnd_row;
   const int32_t* bnd_slot;
@@ -80,10 +79,6 @@ struct merbit_plan_s {
   int32_t* hot_list = nullptr;
   int hot_n = 0;
   double hot_cover = 0.0;                // fraction of the nonzeros in hot columns
-  int hot_max = 0;                       // the table's settings, kept for a rebuild
-  double hot_min_cover = 0.0;
-  int cold_uses = 0;                     // columns used at most this often carry bit 30 in col_hot
-  double cold_cover = 0.0;               // fraction of the nonzeros in such columns
   uint32_t* tile_x = nullptr;
   uint32_t* tile_y = nullptr;
   uint32_t* lane_desc = nullptr;
@@ -110,7 +105,6 @@ struct merbit_plan_s {
     merbit::Geometry g;
     g.tile_x = tile_x; g.tile_y = tile_y; g.lane_desc = lane_desc; g.col = col;
     g.col_stage = col; g.hot_list = hot_list; g.hot_n = 0;   // a launch opts in to the table
-    g.tag_cold = 0;
     g.wait_limit = wait_limit;
     g.bnd_row = bnd_row; g.bnd_slot = bnd_slot;
     g.bnd_acc = bnd_acc; g.part = part; g.red = red;
@@ -213,8 +207,7 @@ cudaError_t ir_apply(const merbit_plan_s* p, double* pi, double* s_out, cudaStre
 
 // Launch configuration of the split kernel's plain product (f32 or f64 values and
 // vectors) for a plan: grid, dynamic shared memory, geometry (with the hot-column table
-// if that launch takes it); false if it cannot be launched.  For f32, a plan set to
-// MERBIT_KERNEL_SPLIT_COLS gives the column-only stages' configuration.
+// if that launch takes it); false if it cannot be launched.
 bool split_config_f32(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem);
 bool split_config_f64(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem);
 
@@ -225,5 +218,9 @@ int persistent_grid(const void* kernel, int threads, size_t smem, size_t smem_ma
 // Dynamic shared memory one CTA of `kernel` may use while `per_sm` of its CTAs stay
 // resident on an SM of the current device (0 on error).
 size_t smem_room(const void* kernel, int per_sm);
+
+// The same room while the SM's shared memory (per_sm CTAs, each with the reserved block
+// share and the kernel's static shared memory) stays at or below shared_per_sm bytes.
+size_t smem_room_below(const void* kernel, int per_sm, size_t shared_per_sm);
 
 }  // namespace merbit

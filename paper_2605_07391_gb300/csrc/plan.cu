@@ -233,4 +233,21 @@ size_t smem_room(const void* kernel, int per_sm) {
   return room > 0 ? (size_t)room : 0;
 }
 
+size_t smem_room_below(const void* kernel, int per_sm, size_t shared_per_sm) {
+  const size_t room = smem_room(kernel, per_sm);
+  if (per_sm <= 0 || room == 0) return 0;
+  int dev = 0, reserved = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+    return 0;
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const long long share = (long long)(shared_per_sm / (size_t)per_sm) - reserved - (long long)fa.sharedSizeBytes;
+  const size_t below = share > 0 ? (size_t)share : 0;
+  return below < room ? below : room;
+}
+
 }  // namespace merbit

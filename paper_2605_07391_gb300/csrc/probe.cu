@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
     __syncthreads();
   }
   constexpr int U = 8;   // gathers in flight per thread
+  const bool hot = g.hot_n > 0;
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   XT acc = XT(0);
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       v[u] = XT(0);
       if (k < g.nnz) {
         const int c = (int)ld_stream(reinterpret_cast<const uint32_t*>(g.col_stage) + k, pol_stream);
-        v[u] = gather_x(g, c, x, tab, pol_x);
+        v[u] = hot ? gather_x<true>(c, x, tab, pol_x) : gather_x<false>(c, x, tab, pol_x);
       }
     }
 #pragma unroll

@@ -18,9 +18,7 @@ cudaError_t spmv_pr_f32(const merbit_plan_s* p, const float* vals, const float* 
 }
 
 bool split_config_f32(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem) {
-  if (p->spmv_kernel == MERBIT_KERNEL_SPLIT_COLS)
-    return split_config<float, float, float, EpiPlain<float, float>, false>(p, g, grid, smem, true);
-  return split_config<float, float, float, EpiPlain<float, float>, true>(p, g, grid, smem, true);
+  return split_config<float, float, float, EpiPlain<float, float>>(p, g, grid, smem, true);
 }
 
 }  // namespace merbit

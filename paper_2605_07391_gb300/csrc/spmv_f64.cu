@@ -27,7 +27,7 @@ cudaError_t spmv_resid_f64(const merbit_plan_s* p, const double* vals, const dou
 }
 
 bool split_config_f64(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem) {
-  return split_config<double, double, double, EpiPlain<double, double>, true>(p, g, grid, smem, true);
+  return split_config<double, double, double, EpiPlain<double, double>>(p, g, grid, smem, true);
 }
 
 }  // namespace merbit

@@ -94,11 +94,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Bring [src, src + bytes) into L2 ahead of use (no shared-memory destination).
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -140,41 +135,20 @@ __device__ __forceinline__ void ld_x_if(double& v, const double* p, bool pred, u
       : "l"(p), "r"((uint32_t)pred), "l"(pol));
 }
 
-// The same gather without an L1 allocation (for columns that are used too rarely to be
-// found in L1 again).
-__device__ __forceinline__ void ld_x_if_na(float& v, const float* p, bool pred, uint64_t pol) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
-      "@q ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %3;\n\t}"
-      : "+f"(v)
-      : "l"(p), "r"((uint32_t)pred), "l"(pol));
-}
-
-__device__ __forceinline__ void ld_x_if_na(double& v, const double* p, bool pred, uint64_t pol) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
-      "@q ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %3;\n\t}"
-      : "+d"(v)
-      : "l"(p), "r"((uint32_t)pred), "l"(pol));
-}
-
-// x[c] for a column c of the (possibly tagged) staged column stream: c < 0 names hot-table
-// slot ~c (shared memory); with tag_cold, bit 30 marks a rarely used column, gathered
-// without an L1 allocation.
-template <typename XT>
-__device__ __forceinline__ XT gather_x(const Geometry& g, int c, const XT* x, const XT* tab, uint64_t pol_x) {
-  const bool hot = c < 0;
-  XT v = XT(0);
-  if (hot) v = tab[~c];
-  if (g.tag_cold) {
-    const bool cold = (c >> 30) & 1;
-    const int cc = c & 0x3FFFFFFF;
-    ld_x_if(v, x + cc, !hot && !cold, pol_x);
-    ld_x_if_na(v, x + cc, !hot && cold, pol_x);
-  } else {
+// x[c] for a column c of the staged column stream.  With a hot-column table (HOT), c < 0
+// names table slot ~c, whose value this CTA holds in shared memory (tab); the other
+// columns are gathered from x in global memory.
+template <bool HOT, typename XT>
+__device__ __forceinline__ XT gather_x(int c, const XT* x, const XT* tab, uint64_t pol_x) {
+  if constexpr (HOT) {
+    const bool hot = c < 0;
+    XT v = XT(0);
+    if (hot) v = tab[~c];
     ld_x_if(v, x + c, !hot, pol_x);
+    return v;
+  } else {
+    return ld_x(x + c, pol_x);
   }
-  return v;
 }
 
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t pol) {
@@ -372,54 +346,24 @@ struct IsUnit : std::false_type {};
 template <typename AT>
 struct IsUnit<UnitVal<AT>> : std::true_type {};
 
-// Stage layout.  VS: the values are staged by bulk copy beside the column indices (else
-// the producers read them from global memory, and the stage holds column indices only).
-// A stage has a value region when values are staged or the matrix is a pattern (the
-// region then holds the products); products go to the value region when it has their
-// width, otherwise over the column indices.
-template <typename VT, bool VS>
-struct HasValRegion {
-  static constexpr bool value = VS || IsUnit<VT>::value;
-};
-template <typename VT, typename AT, bool VS = true>
+// Products go where an input of the same width was staged (the values, or the pattern's
+// product slots), else over the column indices (16-bit values).
+template <typename VT, typename AT>
 struct ProdInVals {
-  static constexpr bool value = HasValRegion<VT, VS>::value && sizeof(VT) == sizeof(AT);
+  static constexpr bool value = sizeof(VT) == sizeof(AT);
 };
 
-template <typename VT, bool VS = true>
+template <typename VT>
 __host__ __device__ inline size_t stage_vals_bytes(int sigma, int W) {
-  return HasValRegion<VT, VS>::value ? round128(sizeof(VT) * (size_t)stage_cap<VT>(sigma, W)) : 0;
+  return round128(sizeof(VT) * (size_t)stage_cap<VT>(sigma, W));
 }
 template <typename VT>
 __host__ __device__ inline size_t stage_col_bytes(int sigma, int W) {
   return round128(sizeof(int32_t) * (size_t)stage_cap<VT>(sigma, W));
 }
-template <typename VT, bool VS = true>
+template <typename VT>
 __host__ __device__ inline size_t stage_bytes(int sigma, int W) {
-  return stage_vals_bytes<VT, VS>(sigma, W) + stage_col_bytes<VT>(sigma, W);
-}
-
-// A value read from global memory by the producers (column-only stages): streamed once,
-// so it bypasses L1 and is marked evict-first in L2.
-__device__ __forceinline__ float ld_val(const float* p, uint64_t pol) {
-  float v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ double ld_val(const double* p, uint64_t pol) {
-  double v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ __nv_bfloat16 ld_val(const __nv_bfloat16* p, uint64_t pol) {
-  unsigned short v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
-  return __ushort_as_bfloat16(v);
-}
-__device__ __forceinline__ __half ld_val(const __half* p, uint64_t pol) {
-  unsigned short v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
-  return __ushort_as_half(v);
+  return stage_vals_bytes<VT>(sigma, W) + stage_col_bytes<VT>(sigma, W);
 }
 
 // A block's coordinate range: nonzeros [xb, xe) and rows [yb, ye] (the tiles'
@@ -432,10 +376,10 @@ struct BlockSpan {
 // The shared-memory stages of a block kernel and the bulk copies that fill them.  Stage
 // s holds a block's values (none for UnitVal) and column indices; the products and the
 // block's row sums later overwrite them in place.
-template <typename VT, typename AT, bool VS = true>
+template <typename VT, typename AT>
 struct Stages {
   static constexpr int VE = 16 / (int)sizeof(VT);   // values per 16 bytes
-  static constexpr bool kStageVals = VS && !IsUnit<VT>::value;   // a value stream is copied
+  static constexpr bool kStageVals = !IsUnit<VT>::value;   // a value stream is copied
   const Geometry& g;
   const VT* vals;
   unsigned char* base;
@@ -444,8 +388,8 @@ struct Stages {
   uint64_t pol;       // L2 policy of the streams
 
   __device__ __forceinline__ Stages(const Geometry& g_, const VT* v, unsigned char* smem, uint64_t p)
-      : g(g_), vals(v), base(smem), svb(stage_vals_bytes<VT, VS>(g_.sigma, g_.W)),
-        stb(stage_bytes<VT, VS>(g_.sigma, g_.W)),
+      : g(g_), vals(v), base(smem), svb(stage_vals_bytes<VT>(g_.sigma, g_.W)),
+        stb(stage_bytes<VT>(g_.sigma, g_.W)),
         nnz_v(g_.nnz & ~(VE - 1)), nnz_c(g_.nnz & ~3), pol(p) {}
 
   __device__ __forceinline__ VT* sv(int s) const { return reinterpret_cast<VT*>(base + (size_t)s * stb); }
@@ -464,7 +408,7 @@ struct Stages {
     StageInfo in;
     in.x_bs = b.xb; in.x_be = b.xe; in.y_bs = (int)b.yb; in.y_be = (int)b.ye;
     in.a0v = b.xb & ~(VE - 1);
-    in.endv = kStageVals ? max(in.a0v, min((b.xe + VE - 1) & ~(VE - 1), nnz_v)) : in.a0v;
+    in.endv = max(in.a0v, min((b.xe + VE - 1) & ~(VE - 1), nnz_v));
     in.a0c = b.xb & ~3;
     in.endc = max(in.a0c, min((b.xe + 3) & ~3, nnz_c));
     *info = in;
@@ -473,18 +417,12 @@ struct Stages {
     mbar_arrive_expect_tx(bar, bv + bc);
     if (bv) bulk_g2s(sv(s), vals + in.a0v, bv, bar, pol);
     if (bc) bulk_g2s(sc(s), g.col_stage + in.a0c, bc, bar, pol);
-    if constexpr (!kStageVals && !IsUnit<VT>::value) {
-      // the producers will read this block's values from global memory: start bringing
-      // them into L2 now, as far ahead as the column indices are copied
-      const int p0 = in.a0v, p1 = max(p0, min((b.xe + VE - 1) & ~(VE - 1), nnz_v));
-      if (p1 > p0) bulk_prefetch_l2(vals + p0, (uint32_t)(p1 - p0) * (uint32_t)sizeof(VT));
-    }
   }
 
   // The stage's product slots (over the values, or over the column indices for 16-bit
   // values) and the nonzero index of slot 0.
   __device__ __forceinline__ AT* prod(int s, const StageInfo& in, int& pb) const {
-    if constexpr (ProdInVals<VT, AT, VS>::value) {
+    if constexpr (ProdInVals<VT, AT>::value) {
       pb = in.a0v;
       return reinterpret_cast<AT*>(sv(s));
     } else {
@@ -493,30 +431,19 @@ struct Stages {
     }
   }
 
-  // x[col] of a staged nonzero k.  A staged column c < 0 names hot-table slot ~c, whose
-  // x value this CTA holds in shared memory (tab); the other columns are gathered from
-  // x in global memory.  Nonzeros past the staged range read the plain column array.
-  template <typename XT>
+  // x[col] of a staged nonzero k (gather_x: from the hot table for a tagged column when
+  // HOT).  Nonzeros past the staged range read the plain column array.
+  template <bool HOT, typename XT>
   __device__ __forceinline__ void gather(int s, const StageInfo& in, int k, const XT* x, const XT* tab,
                                          uint64_t pol_x, AT& xv) const {
     const int c = k < in.endc ? sc(s)[k - in.a0c] : __ldg(g.col + k);
-    xv = static_cast<AT>(gather_x(g, c, x, tab, pol_x));
-  }
-  // the value of nonzero k (1 for a pattern): staged, or read from global memory
-  __device__ __forceinline__ AT value(int s, const StageInfo& in, int k) const {
-    if constexpr (IsUnit<VT>::value) {
-      return AT(1);
-    } else if constexpr (kStageVals) {
-      return static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k]));
-    } else {
-      return static_cast<AT>(widen(ld_val(vals + k, pol)));
-    }
+    xv = static_cast<AT>(gather_x<HOT>(c, x, tab, pol_x));
   }
   __device__ __forceinline__ AT product(int s, const StageInfo& in, int k, AT xv) const {
     if constexpr (IsUnit<VT>::value) {
       return xv;
     } else {
-      return value(s, in, k) * xv;
+      return static_cast<AT>(widen(k < in.endv ? sv(s)[k - in.a0v] : vals[k])) * xv;
     }
   }
 };
@@ -729,20 +656,25 @@ __global__ void __launch_bounds__(kThreads, 3)
     // ---- stage products val * x[col] (load_smem of Algorithm MERBIT SpMV)
     {
       const int cnt = in.x_be - in.x_bs;
-      for (int base = 0; base < cnt; base += kThreads * kSigmaMax) {
-        AT xv[kSigmaMax];
+      auto form_products = [&](auto hot_tag) {
+        constexpr bool HOT = decltype(hot_tag)::value;
+        for (int base = 0; base < cnt; base += kThreads * kSigmaMax) {
+          AT xv[kSigmaMax];
 #pragma unroll
-        for (int u = 0; u < kSigmaMax; ++u) {
-          const int e = base + tid + u * kThreads;
-          xv[u] = AT(0);
-          if (e < cnt) st.gather(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
-        }
+          for (int u = 0; u < kSigmaMax; ++u) {
+            const int e = base + tid + u * kThreads;
+            xv[u] = AT(0);
+            if (e < cnt) st.template gather<HOT>(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
+          }
 #pragma unroll
-        for (int u = 0; u < kSigmaMax; ++u) {
-          const int e = base + tid + u * kThreads;
-          if (e < cnt) prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
+          for (int u = 0; u < kSigmaMax; ++u) {
+            const int e = base + tid + u * kThreads;
+            if (e < cnt) prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
+          }
         }
-      }
+      };
+      if (g.hot_n > 0) form_products(std::true_type{});
+      else form_products(std::false_type{});
     }
     AT* s_y = prod + (in.x_be - pb);
     for (int r = tid; r <= in.y_be - in.y_bs; r += kThreads) s_y[r] = AT(0);
@@ -822,13 +754,12 @@ __device__ __forceinline__ bool consumers_or(bool pred) {
   return r != 0;
 }
 
-template <typename VT, typename XT, typename AT, typename Epi, bool VS = true>
+template <typename VT, typename XT, typename AT, typename Epi>
 __global__ void __launch_bounds__(kSplitThreads, 2)
     merbit_spmv_split_kernel(const Geometry g, const VT* __restrict__ vals, const XT* __restrict__ x,
                           Epi epi) {
-  static_assert(ProdInVals<VT, AT, VS>::value || sizeof(AT) == 4, "product slot width");
-  using St = Stages<VT, AT, VS>;
-  constexpr bool kLoadVals = !St::kStageVals && !IsUnit<VT>::value;   // producers read the values
+  static_assert(ProdInVals<VT, AT>::value || sizeof(AT) == 4, "product slot width");
+  using St = Stages<VT, AT>;
   const int S = g.stages;                              // 2 or 3 stages in the ring
   __shared__ __align__(8) uint64_t full[kSplitStages];   // the stage's bulk copies have landed
   __shared__ __align__(8) uint64_t ready[kSplitStages];  // the stage's products are formed
@@ -894,28 +825,26 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
       // gathers in flight per thread: up to 14 (one block at sigma 14); 10 for 8-byte
       // products, which keeps them in registers (one block at sigma <= 10)
       constexpr int NB = sizeof(AT) == 8 ? 10 : kSigmaMax;
-      for (int base = 0; base < cnt; base += kSplitProducers * NB) {
-        AT xv[NB];
-        AT wv[NB];   // values read from global memory (column-only stages)
+      // the plain gather or the hot-table gather, chosen once per block (uniform)
+      auto form_products = [&](auto hot_tag) {
+        constexpr bool HOT = decltype(hot_tag)::value;
+        for (int base = 0; base < cnt; base += kSplitProducers * NB) {
+          AT xv[NB];
 #pragma unroll
-        for (int u = 0; u < NB; ++u) {
-          const int e = base + pt + u * kSplitProducers;
-          xv[u] = AT(0);
-          wv[u] = AT(0);
-          if (e < cnt) {
-            st.gather(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
-            if constexpr (kLoadVals) wv[u] = st.value(s, in, in.x_bs + e);
+          for (int u = 0; u < NB; ++u) {
+            const int e = base + pt + u * kSplitProducers;
+            xv[u] = AT(0);
+            if (e < cnt) st.template gather<HOT>(s, in, in.x_bs + e, x, tab, pol_x, xv[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < NB; ++u) {
+            const int e = base + pt + u * kSplitProducers;
+            if (e < cnt) prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
           }
         }
-#pragma unroll
-        for (int u = 0; u < NB; ++u) {
-          const int e = base + pt + u * kSplitProducers;
-          if (e < cnt) {
-            if constexpr (kLoadVals) prod[in.x_bs + e - pb] = wv[u] * xv[u];
-            else prod[in.x_bs + e - pb] = st.product(s, in, in.x_bs + e, xv[u]);
-          }
-        }
-      }
+      };
+      if (g.hot_n > 0) form_products(std::true_type{});
+      else form_products(std::false_type{});
       AT* s_y = prod + (in.x_be - pb);
       for (int r = pt; r <= in.y_be - in.y_bs; r += kSplitProducers) s_y[r] = AT(0);
       // these generic writes precede the bulk copy that later refills the stage; one
@@ -1086,28 +1015,35 @@ __global__ void __launch_bounds__(256) merbit_finalize_kernel(const Geometry g, 
 // Launch geometry of one block kernel: the plan's hot-column table is added to the
 // stages' shared memory when the whole table fits without lowering the number of
 // resident CTAs per SM; otherwise the launch streams the plain column array.
+// L1 left beside the shared memory matters below about 60 KB: when the blocks' shared
+// memory per SM crosses the second-largest carveout (196 KB on sm_100-class SMs), the driver
+// takes the largest one and the x gather slows by ~40 % (measured on R-MAT-24).  The
+// table is only added while the SM's shared memory stays at or below that carveout.
+constexpr size_t kSharedPerSmKeepL1 = 196 * 1024;
+
 template <typename XT>
 inline size_t add_hot_table(const merbit_plan_s* p, Geometry& g, const void* kern, size_t stages,
                             int per_sm) {
-  if (!p->col_hot || per_sm <= 0) return stages;
+  if (p->hot_n <= 0 || !p->col_hot || per_sm <= 0) return stages;
   const size_t need = stages + ((sizeof(XT) * (size_t)p->hot_n + 15) & ~size_t(15));
-  if (p->hot_n > 0 && need > smem_room(kern, per_sm)) return stages;
+  if (need > smem_room(kern, per_sm)) return stages;
+  const size_t room_keep_l1 = smem_room_below(kern, per_sm, kSharedPerSmKeepL1);
+  if (need > room_keep_l1 && stages <= room_keep_l1) return stages;   // the table would cost L1
   g.col_stage = p->col_hot;
   g.hot_list = p->hot_list;
   g.hot_n = p->hot_n;
-  g.tag_cold = p->cold_uses > 0;
   return need;
 }
 
 // Grid, dynamic shared memory and geometry (with or without the hot-column table) of the
 // split kernel's launch for a plan; false if two of its CTAs do not fit on an SM (or
 // none does, when `forced`).
-template <typename VT, typename XT, typename AT, typename Epi, bool VS>
+template <typename VT, typename XT, typename AT, typename Epi>
 bool split_config(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem, bool forced) {
-  auto kern = merbit_spmv_split_kernel<VT, XT, AT, Epi, VS>;
+  auto kern = merbit_spmv_split_kernel<VT, XT, AT, Epi>;
   const void* kp = reinterpret_cast<const void*>(kern);
   g.stages = p->spmv_kernel == MERBIT_KERNEL_SPLIT2 ? 2 : kSplitStages;
-  const size_t stages = (size_t)g.stages * stage_bytes<VT, VS>(p->sigma, p->tiles_per_block);
+  const size_t stages = (size_t)g.stages * stage_bytes<VT>(p->sigma, p->tiles_per_block);
   const size_t stages_max = stages;
   grid = persistent_grid(kp, kSplitThreads, stages, stages_max, p->num_sms);
   if (grid <= 0 || (!forced && grid < 2 * p->num_sms)) return false;
@@ -1129,28 +1065,15 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   Geometry g = p->geom();
   int grid = 0;
   bool split = false;
-  // column-only stages need 4-byte products (they are written over the column indices)
-  constexpr bool kColsOk = sizeof(AT) == 4 && !IsUnit<VT>::value;
   const int kind = p->spmv_kernel;
   // A split kernel that was asked for but cannot hold even one CTA's stages on an SM (large
   // sigma x block size with 8-byte values) gives way to the classic kernel, whose ring
   // has two stages.
-  if constexpr (kColsOk) {
-    if (kind == MERBIT_KERNEL_SPLIT_COLS) {
-      size_t smem = 0;
-      split = split_config<VT, XT, AT, Epi, false>(p, g, grid, smem, true);
-      if (split)
-        merbit_spmv_split_kernel<VT, XT, AT, Epi, false><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
-    }
-  }
-  if (split) {
-    // launched above
-  } else if (kind == MERBIT_KERNEL_SPLIT || kind == MERBIT_KERNEL_SPLIT_COLS || kind == MERBIT_KERNEL_SPLIT2 ||
-             (kind == MERBIT_KERNEL_AUTO && sizeof(VT) >= 4)) {
+  if (kind == MERBIT_KERNEL_SPLIT || kind == MERBIT_KERNEL_SPLIT2 ||
+      (kind == MERBIT_KERNEL_AUTO && sizeof(VT) >= 4)) {
     size_t smem = 0;
-    g = p->geom();
-    split = split_config<VT, XT, AT, Epi, true>(p, g, grid, smem, kind != MERBIT_KERNEL_AUTO);
-    if (split) merbit_spmv_split_kernel<VT, XT, AT, Epi, true><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
+    split = split_config<VT, XT, AT, Epi>(p, g, grid, smem, kind != MERBIT_KERNEL_AUTO);
+    if (split) merbit_spmv_split_kernel<VT, XT, AT, Epi><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
   }
   if (!split) {
     g = p->geom();

@@ -21,7 +21,7 @@ F32, F64, BF16, F16 = 0, 1, 2, 3
 PLAIN, IR_BF16, IR_F16, IR_F32 = 0, 1, 2, 3
 STATUS = {0: "OK", 1: "EINVAL", 2: "EOVERFLOW", 3: "ENOMEM", 4: "ECUDA", 5: "ENOTCONV",
           6: "EDEVICE"}
-KERNELS = {"auto": 0, "classic": 1, "split": 2, "split_cols": 3, "split2": 4}
+KERNELS = {"auto": 0, "classic": 1, "split": 2, "split2": 3}
 MODES = {"plain": PLAIN, "ir_bf16": IR_BF16, "ir_f16": IR_F16, "ir_f32": IR_F32}
 _TORCH_DT = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch.float16: F16}
 
@@ -33,7 +33,7 @@ EXPORTS = ["merbit_plan", "merbit_plan_ex", "merbit_plan_destroy", "merbit_plan_
            "merbit_spmv_noalloc_status",
            "merbit_transpose", "merbit_transpose_get", "merbit_transpose_destroy", "merbit_gather",
            "merbit_plan_set_hot_columns", "merbit_gather_probe", "merbit_plan_set_wait_limit",
-           "merbit_autotune", "merbit_plan_set_cold_columns", "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
+           "merbit_autotune", "merbit_sddmm", "merbit_pagerank_adjoint", "merbit_batch_plan", "merbit_batch_pagerank",
            "merbit_batch_get_plan", "merbit_batch_destroy", "merbit_autotune_sigma", "merbit_bicgstab",
            "merbit_last_error",
            "merbit_version"]
@@ -83,7 +83,6 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "merbit_plan_set_kernel": [vp, ctypes.c_int],
             "merbit_gather_probe": [vp, i32, vp, vp, vp],
             "merbit_plan_set_wait_limit": [vp, i32],
-            "merbit_plan_set_cold_columns": [vp, i32, vp, ctypes.POINTER(dbl)],
             "merbit_plan_set_hot_columns": [vp, i32, dbl, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)],
             "merbit_plan_export": [vp, vp, vp, vp, vp],
             "merbit_spmv": [vp, i32, vp, vp, vp],
@@ -224,14 +223,6 @@ class Plan:
     def set_kernel(self, kernel: str):
         """Block kernel for later products: "auto", "classic" or "split"."""
         _check("merbit_plan_set_kernel", load().merbit_plan_set_kernel(self.handle, KERNELS[kernel]))
-
-    def set_cold_columns(self, max_uses: int, stream=None) -> float:
-        """merbit_plan_set_cold_columns: gather columns used at most max_uses times past L1
-        (0 clears).  Returns the fraction of the nonzeros in such columns."""
-        cov = ctypes.c_double(0.0)
-        _check("merbit_plan_set_cold_columns", load().merbit_plan_set_cold_columns(
-            self.handle, int(max_uses), _stream(stream), ctypes.byref(cov)))
-        return cov.value
 
     def set_wait_limit(self, polls: int):
         """merbit_plan_set_wait_limit (test aid): polls of a stage wait before it gives up;

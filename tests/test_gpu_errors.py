@@ -30,7 +30,7 @@ def _setup(kernel, hot):
 
 
 @pytest.mark.parametrize("hot", [False, True])
-@pytest.mark.parametrize("kernel", ["split", "split_cols", "split2", "classic"])
+@pytest.mark.parametrize("kernel", ["split", "split2", "classic"])
 def test_expired_wait_then_recovery_spmv(cuda_device, kernel, hot):
     a, p, _ = _setup(kernel, hot)
     for dtype in (torch.float32, torch.float64):
@@ -49,7 +49,7 @@ def test_expired_wait_then_recovery_spmv(cuda_device, kernel, hot):
         check_rel(as_f64(y), y_ref, d, TOL[dtype], f"after recovery {kernel} {dtype}")
 
 
-@pytest.mark.parametrize("kernel", ["split", "split_cols", "split2", "classic"])
+@pytest.mark.parametrize("kernel", ["split", "split2", "classic"])
 def test_expired_wait_then_recovery_pagerank(cuda_device, kernel):
     a, p, _ = _setup(kernel, True)
     v64 = torch.from_numpy(a.val).cuda()

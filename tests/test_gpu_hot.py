@@ -69,7 +69,7 @@ def test_selection_rule_exact(cuda_device, max_hot):
     assert p.set_hot_columns(0) == (0, 0.0)
 
 
-@pytest.mark.parametrize("kernel", ["split", "split_cols", "split2", "classic"])
+@pytest.mark.parametrize("kernel", ["split", "split2", "classic"])
 @pytest.mark.parametrize("sigma", [14, 10, 7])
 def test_spmv_with_table_both_kernels(cuda_device, kernel, sigma):
     a = inputs.add_hubs(inputs.rmat_uniform(16, 16, 3, 3), 2, 20000, 40000, 5)
@@ -116,7 +116,7 @@ def test_degenerate_tables(cuda_device):
     p, _ = _plan(a)
     n, cover = p.set_hot_columns(16)
     assert n == 3 and cover == 1.0
-    for kernel in ("split", "split_cols", "split2", "classic"):
+    for kernel in ("split", "split2", "classic"):
         p.set_kernel(kernel)
         _spmv_check(p, a, torch.float32, what=f"three columns {kernel}")
     # every column used once: no column qualifies
@@ -150,7 +150,7 @@ def test_full_rmat24_f32_with_table(cuda_device):
     _spmv_check(p, a, torch.float32, what="rmat24 f32 with table")
 
 
-@pytest.mark.parametrize("kernel", ["split", "split_cols"])
+@pytest.mark.parametrize("kernel", ["split", "split2"])
 @pytest.mark.parametrize("max_hot", [0, 3000])
 def test_gather_probe_sums_every_gather(cuda_device, max_hot, kernel):
     """The gather probe loads x[col[k]] once per nonzero (from the table for hot columns):
@@ -166,33 +166,3 @@ def test_gather_probe_sums_every_gather(cuda_device, max_hot, kernel):
         want = float(cnt @ as_f64(x))
         assert abs(float(sink.double().sum()) - want) <= tol * want
 
-
-@pytest.mark.parametrize("kernel", ["split", "split_cols", "split2", "classic"])
-@pytest.mark.parametrize("max_hot", [0, 2000])
-def test_cold_column_marks(cuda_device, kernel, max_hot):
-    """Columns used at most T times are gathered past L1: the marked share of the nonzeros
-    is exact, and every product (with or without the table) matches the oracle."""
-    a = inputs.add_hubs(inputs.rmat_uniform(16, 16, 3, 3), 2, 20000, 40000, 5)
-    p, _ = _plan(a, 14, kernel)
-    p.set_hot_columns(max_hot)
-    cnt = np.bincount(a.col, minlength=a.n_cols)
-    for T in (4, 64):
-        cover = p.set_cold_columns(T)
-        hot_cols = set()
-        if max_hot:
-            n, _ = _expected_table(a, max_hot)
-            hot_cols = set(np.argsort(-cnt, kind="stable")[:n].tolist())
-        cold = (cnt <= T) & (cnt > 0)
-        if hot_cols:
-            cold[list(hot_cols)] = False
-        assert abs(cover - cnt[cold].sum() / a.nnz) < 1e-12
-        for dtype in (torch.float32, torch.float64):
-            _spmv_check(p, a, dtype, what=f"cold<={T} hot={max_hot} {kernel} {dtype}")
-        if kernel != "classic":
-            x = torch.from_numpy(inputs.uniform_vector(a.n_cols, 8)).cuda().float()
-            sink = p.gather_probe(x)
-            torch.cuda.synchronize()
-            want = float(cnt.astype(np.float64) @ as_f64(x))
-            assert abs(float(sink.double().sum()) - want) <= 1e-5 * want
-    assert p.set_cold_columns(0) == 0.0
-    _spmv_check(p, a, torch.float32, what="cold marks cleared")
