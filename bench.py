@@ -752,7 +752,7 @@ def main():
     ap.add_argument("--inner-sweeps", type=int, default=0,
                     help="max inner sweeps per refinement step (0: the tuned setting of each mode)")
     ap.add_argument("--sigma", type=int, default=14, help="steps per lane of the plan")
-    ap.add_argument("--hot", type=int, default=8192,
+    ap.add_argument("--hot", type=int, default=0,
                     help="hot-column table of the plans: up to this many columns (0: none)")
     ap.add_argument("--hot-min-cover", type=float, default=0.05,
                     help="keep a --hot table only if its columns hold this fraction of the nonzeros")

@@ -56,6 +56,7 @@ struct Geometry {
   int W;           // tiles per block
   int stages;      // split kernel: stages in its ring (2 or 3)
   int desc64;      // lane descriptors are 64-bit words (sigma > 14)
+  int fold;        // the block kernel's last CTA finishes the product (few blocks)
   int tile_num;
   int lane_num;
   int nb;          // number of blocks of tiles
@@ -109,7 +110,7 @@ struct merbit_plan_s {
     g.bnd_row = bnd_row; g.bnd_slot = bnd_slot;
     g.bnd_acc = bnd_acc; g.part = part; g.red = red;
     g.n_rows = (int)n_rows; g.nnz = (int)nnz; g.steps = (int)(nnz + n_rows);
-    g.sigma = sigma; g.W = tiles_per_block; g.stages = 3; g.desc64 = desc_bytes == 8;
+    g.sigma = sigma; g.W = tiles_per_block; g.stages = 3; g.desc64 = desc_bytes == 8; g.fold = 0;
     g.tile_num = (int)tile_num; g.lane_num = (int)lane_num; g.nb = (int)nb;
     return g;
   }

@@ -128,12 +128,16 @@ merbit_status merbit_spmv_noalloc(const int32_t* row_ptr, const int32_t* col_idx
   p.bnd_acc = reinterpret_cast<double*>(b + c.off[7]);
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // The array keeps the previous call's contents.  The boundary accumulators
-  // must start at zero (a call whose kernel gave up may have left some set).
+  // The array keeps the previous call's contents.  The boundary accumulators and
+  // the arrival count must start at zero (a call whose kernel gave up may have left
+  // them set).
   // The error word at the start of the array is left alone: it is zero when
   // the library loads, a kernel that gives up on a bounded wait sets it, and
   // only merbit_spmv_noalloc_status reads and clears it.
   cudaError_t e = cudaMemsetAsync(p.bnd_acc, 0, sizeof(double) * (size_t)(p.nb + 1), st);
+  // a small product is finished by the last CTA to arrive; a call whose kernel gave up
+  // may have left the arrival count behind
+  if (e == cudaSuccess) e = cudaMemsetAsync(&p.red->arrive, 0, sizeof(p.red->arrive), st);
   if (e == cudaSuccess) e = build_tiles(&p, row_ptr, st);
   if (e == cudaSuccess) e = spmv_plain_f32(&p, vals, x, y, st);
   if (e != cudaSuccess) return noalloc_fail(MERBIT_ECUDA, cudaGetErrorString(e));

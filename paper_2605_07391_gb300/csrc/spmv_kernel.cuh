@@ -485,6 +485,8 @@ __device__ __forceinline__ uint64_t ld_desc(const Geometry& g, int j, uint64_t p
   return ld_stream(g.lane_desc + j, pol);
 }
 
+constexpr int kSplitThreadsMax = 512;   // the largest block of the SpMV kernels
+
 // One warp reduces one tile of a staged block into the block's row sums (Algorithm
 // tile_normal_tackle with WarpSegmentedSum; tile_fast_tackle for a tile marked as part
 // of a single row).  pt: the tile's first product; sy: the row sums from the tile's first
@@ -571,6 +573,56 @@ __device__ __forceinline__ void reduce_tile(const Geometry& g, const AT* pt, AT*
   const AT seg = __shfl_sync(0xffffffffu, sv_, src);
   const int row = __shfl_sync(0xffffffffu, yo, src);
   if (head) atomicAdd(sy + row, seg);
+}
+
+// The second pass of a small product run by the block kernel itself: the CTA that
+// finishes last (an arrival count after a fence) writes the rows shared between blocks
+// and sums the per-CTA partials in a fixed order, then calls the epilogue's finish.
+// Used when the product has few blocks (`g.fold`), where a second launch would cost
+// more than the work; all threads of the CTA call it.
+template <typename Epi>
+__device__ __forceinline__ void fold_finalize(const Geometry& g, const Epi& epi) {
+  __shared__ int last;
+  __shared__ double fold_smem[kSplitThreadsMax / 32][2];
+  const int tid = threadIdx.x;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(&g.red->arrive, 1u) + 1 == gridDim.x;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double p0 = 0.0, p1 = 0.0;
+  for (int k = tid; k <= g.nb; k += blockDim.x) {
+    if (__ldg(g.bnd_slot + k) != k) continue;
+    const int r = __ldg(g.bnd_row + k);
+    if (r >= g.n_rows) continue;
+    epi.row64(r, read_reset(g.bnd_acc + k), p0, p1);
+  }
+  if constexpr (Epi::kReduce) {
+    for (int i = tid; i < (int)gridDim.x; i += blockDim.x) {
+      const double2 q = __ldcg(g.part + i);
+      p0 += q.x;
+      p1 += q.y;
+    }
+    p0 = warp_sum(p0);
+    p1 = warp_sum(p1);
+    if ((tid & 31) == 0) {
+      fold_smem[tid >> 5][0] = p0;
+      fold_smem[tid >> 5][1] = p1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+        a += fold_smem[w][0];
+        b += fold_smem[w][1];
+      }
+      epi.finish(a, b, g.red);
+    }
+  }
+  if (tid == 0) g.red->arrive = 0u;
 }
 
 template <typename VT, typename XT, typename AT, typename Epi>
@@ -722,6 +774,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       g.part[blockIdx.x] = make_double2(a, b);
     }
   }
+  if (g.fold) fold_finalize(g, epi);
 }
 
 // ---------------------------------------------------------------- warp-specialized kernel
@@ -938,6 +991,9 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
   __syncthreads();
   if (tid == 0 && failed)
     for (int k = max(0, issued - S); k < issued; ++k) mbar_wait_bounded(&full[k % S], (uint32_t)(k / S) & 1u);
+  // a CTA that gave up does not arrive, so no CTA finishes the product (the error bit
+  // tells the host)
+  if (g.fold && !failed) fold_finalize(g, epi);
 }
 
 // Grid-wide FP64 sums of (p0, p1) over a launch of blockDim.x <= 256 threads:
@@ -1012,6 +1068,9 @@ __global__ void __launch_bounds__(256) merbit_finalize_kernel(const Geometry g, 
   }
 }
 
+// Products of at most this many blocks are finished by the block kernel's last CTA.
+constexpr int64_t kFoldMaxBlocks = 1024;
+
 // Launch geometry of one block kernel: the plan's hot-column table is added to the
 // stages' shared memory when the whole table fits without lowering the number of
 // resident CTAs per SM; otherwise the launch streams the plain column array.
@@ -1043,9 +1102,16 @@ bool split_config(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem, 
   auto kern = merbit_spmv_split_kernel<VT, XT, AT, Epi>;
   const void* kp = reinterpret_cast<const void*>(kern);
   g.stages = p->spmv_kernel == MERBIT_KERNEL_SPLIT2 ? 2 : kSplitStages;
-  const size_t stages = (size_t)g.stages * stage_bytes<VT>(p->sigma, p->tiles_per_block);
+  size_t stages = (size_t)g.stages * stage_bytes<VT>(p->sigma, p->tiles_per_block);
+  grid = persistent_grid(kp, kSplitThreads, stages, stages, p->num_sms);
+  if (!forced && grid < 2 * p->num_sms && g.stages == kSplitStages) {
+    // the automatic choice: when three stages leave room for one CTA per SM only (8-byte
+    // values at large sigma), a ring of two stages may still fit two
+    g.stages = 2;
+    stages = 2 * stage_bytes<VT>(p->sigma, p->tiles_per_block);
+    grid = persistent_grid(kp, kSplitThreads, stages, stages, p->num_sms);
+  }
   const size_t stages_max = stages;
-  grid = persistent_grid(kp, kSplitThreads, stages, stages_max, p->num_sms);
   if (grid <= 0 || (!forced && grid < 2 * p->num_sms)) return false;
   smem = add_hot_table<XT>(p, g, kp, stages, grid / p->num_sms);
   if (smem != stages) grid = persistent_grid(kp, kSplitThreads, smem, std::max(smem, stages_max), p->num_sms);
@@ -1063,6 +1129,8 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   // on an SM (measured on sm_103a, R-MAT scale 21 and 24: 15-30 % faster than the classic
   // kernel there, slower with one CTA per SM, level for 16-bit values).
   Geometry g = p->geom();
+  // few blocks: the block kernel finishes the product itself (no second launch)
+  g.fold = p->nb <= kFoldMaxBlocks;
   int grid = 0;
   bool split = false;
   const int kind = p->spmv_kernel;
@@ -1077,6 +1145,7 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   }
   if (!split) {
     g = p->geom();
+    g.fold = p->nb <= kFoldMaxBlocks;
     auto kern = merbit_spmv_kernel<VT, XT, AT, Epi>;
     const void* kp = reinterpret_cast<const void*>(kern);
     const size_t stages = 2 * stage_bytes<VT>(p->sigma, p->tiles_per_block);
@@ -1091,7 +1160,7 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
     kern<<<grid, kThreads, smem, st>>>(g, vals, x, epi);
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || g.fold) return e;
   const int fgrid = (int)std::min<int64_t>((p->nb + 1 + 255) / 256, (int64_t)p->num_sms * 4);
   merbit_finalize_kernel<Epi><<<fgrid, 256, 0, st>>>(g, epi, Epi::kReduce ? grid : 0);
   return cudaGetLastError();
