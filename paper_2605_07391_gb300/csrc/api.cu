@@ -127,6 +127,7 @@ __global__ void pr_state_init_kernel(double* hist, double d0, RedState* red) {
   red->iters = 0;
   red->inner_done = 0;
   red->launches = 0;
+  red->delta = nullptr;   // published again by this solve's first residual pass
 }
 
 // Correctly rounded (ties to even) float64 -> IEEE binary format with E

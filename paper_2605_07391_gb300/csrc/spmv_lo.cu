@@ -21,7 +21,11 @@ __global__ void __launch_bounds__(256) ir_apply_kernel(double* __restrict__ pi, 
                                                        const uint32_t* __restrict__ dang,
                                                        RedState* red, double* s_out) {
   if (*reinterpret_cast<const volatile int*>(&red->done)) return;
+  // the latest inner iterate is published by the finishing pass of the residual or sweep
+  // launches; after a kernel gave up (error bit set) it may never have been published
+  if (*reinterpret_cast<const volatile int*>(&red->err)) return;
   const float* delta = *reinterpret_cast<const float* const volatile*>(&red->delta);
+  if (delta == nullptr) return;
   double p0 = 0.0, p1 = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double d = static_cast<double>(delta[i]);
