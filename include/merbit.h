@@ -325,7 +325,7 @@ merbit_status merbit_autotune_sigma(const int32_t* row_ptr, const int32_t* col_i
 
 /*
  * merbit_autotune — picks a plan's parameters for one matrix and value type by
- * measurement: every combination of sigma (sigmas[n_sigma], each in [1, 14]), tiles per
+ * measurement: every combination of sigma (sigmas[n_sigma], each in [1, 42]), tiles per
  * block (blocks[n_block], each 4, 8 or 16), block kernel (kernels[n_kernel], each a
  * MERBIT_KERNEL_* value) and hot-column table size (hots[n_hot], each in [0, 2^20];
  * merbit_plan_set_hot_columns with min_cover 0) is built and timed: one warm-up product
