@@ -18,6 +18,13 @@ cudaError_t spmv_pr_f32(const merbit_plan_s* p, const float* vals, const float* 
 }
 
 bool split_config_f32(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem) {
+  // the launch the product itself makes (the automatic choice may take a two-stage ring);
+  // when the product would fall back to the classic kernel, the split kernel's own launch
+  const Geometry g0 = g;
+  if (split_config<float, float, float, EpiPlain<float, float>>(p, g, grid, smem, p->spmv_kernel != MERBIT_KERNEL_SPLIT &&
+                                                              p->spmv_kernel != MERBIT_KERNEL_SPLIT2))
+    return true;
+  g = g0;
   return split_config<float, float, float, EpiPlain<float, float>>(p, g, grid, smem, true);
 }
 
