@@ -341,7 +341,7 @@ class Batch:
         return self._handle
 
     def set_kernel(self, kernel: str):
-        """Block kernel of the batch's plan: "auto", "classic", "split" or "split_cols" (the
+        """Block kernel of the batch's plan: "auto", "classic", "split" or "split2" (the
         solve is recorded again at the next call)."""
         h = ctypes.c_void_p(load().merbit_batch_get_plan(self.handle))
         _check("merbit_plan_set_kernel", load().merbit_plan_set_kernel(h, KERNELS[kernel]))
