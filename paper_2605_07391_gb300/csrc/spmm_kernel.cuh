@@ -5,23 +5,29 @@
 // Work unit: the SpMV's block of 8 tiles, staged by the same two bulk copies;
 // one warp per tile.  A column chunk of KC columns is split into slices of VW
 // consecutive columns (VW = 4: one 16-byte load per slice); T = KC / VW
-// threads cover a chunk, so the warp forms 32 / T groups.
-//   1. The warp decodes its tile's lane descriptors (Sec. 4.1.1 bit_flag):
-//      every down step ends a row, at the tile-relative nonzero position
-//      x_off + (right steps before it); a warp scan of the down-step counts
-//      lays these row ends out in shared memory in row order.
-//   2. Group g takes an equal share [t0, t1) of the tile's nonzeros and the
-//      row ends at positions in (t0, t1] (group 0 also those at 0).  It
-//      gathers U row slices X[col[p], c..c+VW) at a time, independent of row
-//      ends, then adds vals[p] * slice into the running row sum, closing a row
-//      whenever the next row end is reached.
-//   3. Rows that begin and end inside a group's share are written directly;
-//      the first and last partial row of every share go to a small shared
-//      table.  After a block barrier each group adds up the table entries of
-//      the rows its own entries start; rows inside the block are written and
-//      the block's first and last rows are added into per-row FP64
-//      accumulators that a finalize kernel writes out and clears (the SpMV's
-//      boundary-row scheme, KC values wide).
+// threads cover a chunk, so a warp walks L = 32 / T lanes at once and a tile's
+// 32 lanes in T passes.
+//   1. A thread takes one lane of the pass and one slice.  The lane descriptor
+//      (Sec. 4.1.1 bit_flag) gives, for every step, whether it is a down step
+//      and which nonzero a right step consumes (step k takes nonzero
+//      x_off + k - (down steps before k)), so the row slices of all the lane's
+//      right steps are gathered before any is used.
+//   2. The steps are walked in order: a right step adds vals[p] * slice into
+//      the running sum, a down step ends a row.  Rows ended after the lane's
+//      first down step lie wholly inside the lane and are written to Y; the
+//      lane's first ended row may have begun in earlier lanes.
+//   3. Runs across lanes: the sum open after lane l obeys
+//      OC_l = a_l + b_l * OC_{l-1} (a_l the lane's trailing sum, b_l = 1 when
+//      the lane ends no row), a linear recurrence scanned by shuffles; the
+//      first ended row of lane l totals OC_{l-1} plus the lane's head sum, and
+//      the run open after a pass is carried into the next.
+//   4. The tile's first row and the run open at its end go to a small shared
+//      table; after a block barrier the warp holding a row's first entry adds
+//      its entries.  The block's first and last rows are added into per-row
+//      FP64 accumulators that a finalize kernel writes out and clears (the
+//      SpMV's boundary-row scheme, KC values wide).
+// Single-row tiles (the tile_y mark of Sec. 4.1.2) skip the descriptors: lanes
+// take every L-th nonzero and their sums are added across the warp.
 #pragma once
 
 #include <climits>
@@ -44,6 +50,12 @@ template <> struct SpmmVec<1> {
   static __device__ __forceinline__ void add(T& s, const T& x) { s += x; }
   static __device__ __forceinline__ T shfl_up(const T& v, int d) {
     return __shfl_up_sync(0xffffffffu, v, d);
+  }
+  static __device__ __forceinline__ T shfl_xor(const T& v, int d) {
+    return __shfl_xor_sync(0xffffffffu, v, d);
+  }
+  static __device__ __forceinline__ T shfl(const T& v, int src) {
+    return __shfl_sync(0xffffffffu, v, src);
   }
 };
 template <> struct SpmmVec<4> {
@@ -77,6 +89,14 @@ template <> struct SpmmVec<4> {
     return make_float4(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
                        __shfl_up_sync(0xffffffffu, v.z, d), __shfl_up_sync(0xffffffffu, v.w, d));
   }
+  static __device__ __forceinline__ T shfl_xor(const T& v, int d) {
+    return make_float4(__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d),
+                       __shfl_xor_sync(0xffffffffu, v.z, d), __shfl_xor_sync(0xffffffffu, v.w, d));
+  }
+  static __device__ __forceinline__ T shfl(const T& v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+  }
 };
 
 // Epilogue of the SpMM: Y[r, c..c+VW) = scale * (A X)[r, c..c+VW).  row() takes f32 row sums
@@ -108,24 +128,20 @@ struct SpmmGeometry {
   int kc;           // columns in this chunk (a multiple of VW)
 };
 
-// Two CTAs per SM: the register room (up to 128 per thread) keeps a whole batch of gathers
-// in flight; capping registers for three CTAs per SM serialised them (k = 8: 1.04 ms vs
-// 0.67 ms on R-MAT scale 22).
+// Two CTAs per SM: the register room (up to 128 per thread) holds a lane's sigma row
+// slices in flight.
 template <int KC, int VW, typename Epi>
 __global__ void __launch_bounds__(kThreads, 2)
     merbit_spmm_kernel(const Geometry g, const SpmmGeometry sg, const float* __restrict__ vals,
                        const float* __restrict__ X, int ldx, Epi epi) {
   using V = SpmmVec<VW>;
   using VT = typename V::T;
-  constexpr int T = KC / VW;                   // threads per chunk row
-  constexpr int GRP = 32 / T;                  // groups per warp
-  constexpr int U = VW == 4 ? (KC == 32 ? 12 : 8) : 16;   // row slices gathered per batch
+  constexpr int T = KC / VW;                   // threads per lane, one slice of VW columns each
+  constexpr int L = 32 / T;                    // lanes walked at once (one pass)
+  constexpr int U1 = 8;                        // row slices per round of a single-row tile
   constexpr int VE = 4;
-  constexpr int kEnds = kOmega * kSigmaMax;    // most row ends in one tile
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ StageInfo info[2];
-  __shared__ uint16_t rend_s[kTilesPerBlock][kEnds];
-  __shared__ __align__(16) float head_s[kThreads][VW];           // each thread's head partial
   __shared__ int wt_row[2][2 * kTilesPerBlock];                   // per-warp first / last runs
   __shared__ __align__(16) float wt_val[2][2 * kTilesPerBlock][KC];
   extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -133,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  const int grp = lane / T;
+  const int gl = lane / T;                     // lane of the pass this thread walks
   const int c = (lane % T) * VW;               // first column of this thread's slice
   const bool c_ok = c < sg.kc;
   const int G = gridDim.x;
@@ -145,7 +161,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   auto sc = [&](int s) { return reinterpret_cast<int32_t*>(dyn_smem + (size_t)s * stb + svb); };
   const uint64_t pol_stream = policy_evict_first();
   const int nnz_a = g.nnz & ~(VE - 1);
-  uint16_t* rend = rend_s[warp];
 
   auto geom_of = [&](int v, int& xb, int& xe, uint32_t& yb, uint32_t& ye) {
     const int bs = v * kTilesPerBlock;
@@ -189,33 +204,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     const uint32_t par = (it >> 1) & 1;
     const int ti = v * kTilesPerBlock + warp;
     const bool tile_ok = ti < g.tile_num;
-    int txs = 0, ntile = 0, y_ws = 0, ndown = 0;
+    // the tile's bounds and its 32 lane descriptors (one per thread), read before the
+    // stage wait so that their latency hides behind it
+    uint32_t txs = 0, txe = 0, tys = 0, dreg = 0;
     if (tile_ok) {
-      // 1. row ends of the tile from the lane descriptors
-      txs = (int)__ldg(g.tile_x + ti);
-      ntile = (int)__ldg(g.tile_x + ti + 1) - txs;
-      y_ws = (int)(__ldg(g.tile_y + ti) & ~kMsb);
+      txs = __ldg(g.tile_x + ti);
+      txe = __ldg(g.tile_x + ti + 1);
+      tys = __ldg(g.tile_y + ti);
       const int j = ti * kOmega + lane;
-      uint32_t dm = 0, xo = 0;
-      if (j < g.lane_num) {
-        const uint32_t d = ld_stream(g.lane_desc + j, pol_stream);
-        const int len = min(g.sigma, g.steps - j * g.sigma);
-        dm = (d >> 18) & ((1u << len) - 1u);
-        xo = d & 511u;
-      }
-      const int nd = __popc(dm);
-      int off = nd;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, off, o);
-        if (lane >= o) off += t;
-      }
-      ndown = __shfl_sync(0xffffffffu, off, 31);
-      off -= nd;
-      for (uint32_t m = dm; m; m &= m - 1) {
-        const int k = __ffs(m) - 1;
-        rend[off++] = (uint16_t)(xo + k - __popc(dm & ((1u << k) - 1u)));
-      }
+      if (j < g.lane_num) dreg = ld_stream(g.lane_desc + j, pol_stream);
     }
     int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
     const bool refill = (tid == 0) && (v + 2 * G < g.nb);
@@ -231,104 +228,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     const StageInfo in = info[s];
     const float* vs = sv(s);
     const int32_t* cs = sc(s);
-    const bool staged = in.endv >= in.x_be;      // false only in the block holding the array's tail
-
-    // 2. group grp's share of the tile
-    int head_row = -1, tail_row = -1;
-    VT sum = V::zero();
-    if (tile_ok) {
-      const int t0 = (int)(((long long)grp * ntile) / GRP);
-      const int t1 = (int)(((long long)(grp + 1) * ntile) / GRP);
-      // first owned row end: the number of ends at positions <= t0 (none owned for group 0)
-      auto count_le = [&](int t) {
-        int lo = 0, hi = ndown;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if ((int)rend[mid] <= t) lo = mid + 1; else hi = mid;
-        }
-        return lo;
-      };
-      int q = grp == 0 ? 0 : count_le(t0);
-      const int q1 = count_le(t1);
-      int next = q < q1 ? (int)rend[q] : INT_MAX;
-      bool first = true;
-      auto close_row = [&]() {
-        if (first) {                  // the row may have begun before this share
-          head_row = y_ws + q;
-#pragma unroll
-          for (int k = 0; k < VW; ++k) head_s[tid][k] = V::get(sum, k);
-          first = false;
-        } else if (c_ok) {
-          epi.row(y_ws + q, c, sum);  // begun and ended inside the share
-        }
-        sum = V::zero();
-        ++q;
-        next = q < q1 ? (int)rend[q] : INT_MAX;
-      };
-      const int ib = txs - in.a0v;    // staged index of the tile's first nonzero
-      // U row slices from nonzero base on: ST = the block is fully staged, TAIL = the batch
-      // may run past t1
-      auto batch = [&](int base, auto st_tag, auto tail_tag) {
-        constexpr bool ST = decltype(st_tag)::value;
-        constexpr bool TAIL = decltype(tail_tag)::value;
-        VT xv[U];
-        float wv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          xv[u] = V::zero();
-          wv[u] = 0.f;
-          if ((!TAIL || base + u < t1) && c_ok) {
-            const int i = ib + base + u;
-            int cc;
-            if (ST || in.a0v + i < in.endv) {
-              cc = cs[i];
-              wv[u] = vs[i];
-            } else {
-              cc = __ldg(g.col + in.a0v + i);
-              wv[u] = __ldg(vals + in.a0v + i);
-            }
-            xv[u] = V::load(X + (size_t)cc * ldx + c);
-          }
-        }
-        if (next < base + U) {
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            while (next == base + u) close_row();   // rows ending before nonzero base + u
-            V::fma(wv[u], xv[u], sum);
-          }
-        } else {
-#pragma unroll
-          for (int u = 0; u < U; ++u) V::fma(wv[u], xv[u], sum);
-        }
-      };
-      using yes = std::integral_constant<bool, true>;
-      using no = std::integral_constant<bool, false>;
-      int base = t0;
-      if (staged) {
-#pragma unroll 1
-        for (; base + U <= t1; base += U) batch(base, yes{}, no{});
-        if (base < t1) batch(base, yes{}, yes{});
-      } else {
-#pragma unroll 1
-        for (; base < t1; base += U) batch(base, no{}, yes{});
-      }
-      while (next == t1) close_row();             // rows ending after the share's last nonzero
-      if (first) {
-        head_row = y_ws + q;          // no row ends in this share
-      } else {
-        tail_row = y_ws + q;          // the row in progress continues past the share
-      }
-    }
-    if (tile_ok && tail_row < 0) {
-#pragma unroll
-      for (int k = 0; k < VW; ++k) head_s[tid][k] = V::get(sum, k);   // no row ends in the share
-    }
-
-    // 3a. the warp's shares in order: a segmented sum over the groups' runs, by shuffles.
-    //     Group g holds one run (head_row) or two (head_row < tail_row); the run of its
-    //     last row continues into group g + 1 when that group's head_row is the same row.
-    //     OC_g = total of group g's last-row run up to g obeys OC_g = a_g + b_g * OC_{g-1},
-    //     a linear recurrence scanned in log2(GRP) steps.
     int* wrow = wt_row[s];
     float (*wval)[KC] = wt_val[s];
     if (lane == 0) {
@@ -336,42 +235,21 @@ __global__ void __launch_bounds__(kThreads, 2)
       wrow[2 * warp + 1] = -1;
     }
     __syncwarp();
+
     if (tile_ok) {
-      VT hv;
-      {
-        float h[VW];
-#pragma unroll
-        for (int k = 0; k < VW; ++k) h[k] = head_s[tid][k];
-        hv = V::from(h);
-      }
-      const bool single = tail_row < 0;
-      const int row_out = single ? head_row : tail_row;
-      const int prev_out = __shfl_up_sync(0xffffffffu, row_out, T);
-      const int next_head = __shfl_down_sync(0xffffffffu, head_row, T);
-      const int warp_first = __shfl_sync(0xffffffffu, head_row, 0);
-      VT A = single ? hv : sum;
-      int B = (single && grp > 0 && prev_out == head_row) ? 1 : 0;
-#pragma unroll
-      for (int d = 1; d < GRP; d <<= 1) {
-        const VT Ap = V::shfl_up(A, d * T);
-        const int Bp = __shfl_up_sync(0xffffffffu, B, d * T);
-        if (grp >= d) {
-          if (B) V::add(A, Ap);
-          B &= Bp;
-        }
-      }
-      const VT oc_prev = V::shfl_up(A, T);     // OC_{g-1}
-      VT first_tot = hv;
-      if (grp > 0 && prev_out == head_row) V::add(first_tot, oc_prev);
-      // a finished run: boundary rows of the block go to the FP64 accumulators, the
-      // warp's first run to the cross-warp table, any other row straight to Y
+      const int y_ws = (int)(tys & ~kMsb);
+      const int ntile = (int)(txe - txs);
+      const int ib = (int)txs - in.a0v;          // staged index of the tile's first nonzero
+      // a finished run of row r: block boundary rows go to the FP64 accumulators, the
+      // tile's first row and its run open at the tile's end to the cross-warp table,
+      // any other row straight to Y
       auto emit = [&](int r, const VT& val, bool last_of_warp) {
         if (r >= g.n_rows || !c_ok) return;
         if (r == in.y_bs || r == in.y_be) {
           double* a = sg.acc + (size_t)__ldg(g.bnd_slot + (r == in.y_bs ? v : v + 1)) * KC + c;
 #pragma unroll
           for (int k = 0; k < VW; ++k) atomicAdd(a + k, (double)V::get(val, k));
-        } else if (last_of_warp || r == warp_first) {
+        } else if (last_of_warp || r == y_ws) {
           const int e = 2 * warp + (last_of_warp ? 1 : 0);
           if (lane % T == 0) wrow[e] = r;
 #pragma unroll
@@ -380,18 +258,124 @@ __global__ void __launch_bounds__(kThreads, 2)
           epi.row(r, c, val);
         }
       };
-      const bool last_grp = grp == GRP - 1;
-      if (!single || (!last_grp && next_head != head_row)) emit(head_row, first_tot, false);
-      if (!single && !last_grp && next_head != tail_row) emit(tail_row, sum, false);
-      if (last_grp) emit(row_out, single ? first_tot : sum, true);
+      // the tile's nonzeros, ST = every one of them is staged (false only in the block
+      // holding the array's last few nonzeros, which are read from global memory)
+      auto walk = [&](auto st_tag) {
+        constexpr bool ST = decltype(st_tag)::value;
+        auto gather = [&](int idx, float& w) -> VT {
+          const int i = ib + idx;
+          int cc;
+          if (ST || in.a0v + i < in.endv) {
+            cc = cs[i];
+            w = vs[i];
+          } else {
+            cc = __ldg(g.col + in.a0v + i);
+            w = __ldg(vals + in.a0v + i);
+          }
+          return V::load(X + (size_t)cc * ldx + c);
+        };
+        if (tys & kMsb) {
+          // single-row tile: every nonzero belongs to row y_ws; lane gl takes every
+          // L-th one, then the lanes' sums are added across the warp
+          VT sum = V::zero();
+#pragma unroll 1
+          for (int base = gl; base < ntile; base += L * U1) {
+            VT xv[U1];
+            float wv[U1];
+#pragma unroll
+            for (int u = 0; u < U1; ++u) {
+              xv[u] = V::zero();
+              wv[u] = 0.f;
+              if (base + u * L < ntile && c_ok) xv[u] = gather(base + u * L, wv[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U1; ++u) V::fma(wv[u], xv[u], sum);
+          }
+#pragma unroll
+          for (int o = T; o < 32; o <<= 1) V::add(sum, V::shfl_xor(sum, o));
+          if (gl == 0) emit(y_ws, sum, true);
+          return;
+        }
+        // lane walk (Sec. 4.2, k values wide): T passes of L lanes; each thread issues the
+        // row-slice gathers of all its lane's right steps before using any (the step ->
+        // nonzero map comes from the descriptor alone), then walks the steps: a down step
+        // ends a row.  A lane's first ended row may have begun in earlier lanes, so its
+        // head partial joins the runs flowing in; rows ended later in the lane are whole.
+        VT carry = V::zero();                    // run open after the previous pass
+        int open_row = y_ws;
+#pragma unroll 1
+        for (int p = 0; p < T; ++p) {
+          const int l = p * L + gl;
+          const uint32_t d = __shfl_sync(0xffffffffu, dreg, l);
+          const int j = ti * kOmega + l;
+          const bool active = j < g.lane_num;
+          const int len = active ? min(g.sigma, g.steps - j * g.sigma) : 0;
+          const uint32_t valid = (1u << len) - 1u;
+          const uint32_t dm = (d >> 18) & valid;   // down steps
+          const uint32_t rm = ~(d >> 18) & valid;  // right steps
+          const int xo = (int)(d & 511u);
+          const int y0 = active ? (int)((d >> 9) & 511u) : (g.n_rows - y_ws);
+          VT xv[kSigmaMax];
+          float wv[kSigmaMax];
+#pragma unroll
+          for (int k = 0; k < kSigmaMax; ++k) {
+            xv[k] = V::zero();
+            wv[k] = 0.f;
+            if (((rm >> k) & 1u) && c_ok)
+              xv[k] = gather(xo + k - __popc(dm & ((1u << k) - 1u)), wv[k]);
+          }
+          VT sum = V::zero(), head = V::zero();
+#pragma unroll
+          for (int k = 0; k < kSigmaMax; ++k) {
+            V::fma(wv[k], xv[k], sum);           // zero at down steps and past the lane
+            if ((dm >> k) & 1u) {
+              const int nd = __popc(dm & ((1u << k) - 1u));
+              if (nd == 0) head = sum;
+              else if (c_ok) epi.row(y_ws + y0 + nd, c, sum);
+              sum = V::zero();
+            }
+          }
+          // runs across the pass's lanes: OC_l = run open after lane l obeys
+          // OC_l = a_l + b_l * OC_{l-1} (a_l = the lane's trailing sum, b_l = 1 when the
+          // lane ends no row), with OC_{-1} = carry; scanned in log2(L) shuffle steps
+          const bool hd = dm != 0u;
+          VT A = sum;
+          int B = hd ? 0 : 1;
+          if (gl == 0) {
+            if (B) V::add(A, carry);
+            B = 0;
+          }
+#pragma unroll
+          for (int dd = 1; dd < L; dd <<= 1) {
+            const VT Ap = V::shfl_up(A, dd * T);
+            const int Bp = __shfl_up_sync(0xffffffffu, B, dd * T);
+            if (gl >= dd) {
+              if (B) V::add(A, Ap);
+              B &= Bp;
+            }
+          }
+          const VT up = V::shfl_up(A, T);
+          if (hd) {
+            VT tot = head;
+            V::add(tot, gl == 0 ? carry : up);
+            emit(y_ws + y0, tot, false);
+          }
+          const int src = (L - 1) * T + (lane % T);
+          carry = V::shfl(A, src);
+          open_row = y_ws + __shfl_sync(0xffffffffu, y0 + __popc(dm), src);
+        }
+        if (gl == L - 1) emit(open_row, carry, true);
+      };
+      if (in.endv >= in.x_be) walk(std::integral_constant<bool, true>{});
+      else walk(std::integral_constant<bool, false>{});
     }
     fence_proxy_async_smem();
     __syncthreads();
     if (refill) issue(s, nxb, nxe, nyb, nye);
 
-    // 3b. rows spread over several warps of the block (never a boundary row): the warp
-    //     holding a row's first table entry adds up its entries
-    if (grp == 0) {
+    // rows spread over several warps of the block (never a boundary row): the warp
+    // holding a row's first table entry adds up its entries
+    if (gl == 0) {
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
         const int e = 2 * warp + h;
