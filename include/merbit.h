@@ -182,7 +182,7 @@ merbit_status merbit_gather_probe(merbit_plan_t plan, merbit_dtype xdt, const vo
                                   void* stream);
 
 /* Test aid (no counterpart in the paper): the number of polls after which a stage wait
- * of the plan's SpMV block kernels gives up (polls < 0 restores the default, 2^22).  A
+ * of the plan's SpMV and SpMM block kernels gives up (polls < 0 restores the default, 2^22).  A
  * wait that gives up sets the plan's error bit; the kernel then waits, with the default
  * limit, for its own copies in flight and returns, and merbit_plan_sync (or the next
  * solver call) reports MERBIT_EDEVICE and clears the state.  polls = 0 makes every

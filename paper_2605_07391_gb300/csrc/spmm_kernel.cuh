@@ -22,10 +22,11 @@
 //      first ended row of lane l totals OC_{l-1} plus the lane's head sum, and
 //      the run open after a pass is carried into the next.
 //   4. The tile's first row and the run open at its end go to a small shared
-//      table; after a block barrier the warp holding a row's first entry adds
-//      its entries.  The block's first and last rows are added into per-row
-//      FP64 accumulators that a finalize kernel writes out and clears (the
-//      SpMV's boundary-row scheme, KC values wide).
+//      table; the last warp to finish the block (an arrival count, no block
+//      barrier) adds up each row's entries and refills the block's stage.  The
+//      block's first and last rows are added into per-row FP64 accumulators
+//      that a finalize kernel writes out and clears (the SpMV's boundary-row
+//      scheme, KC values wide).
 // Single-row tiles (the tile_y mark of Sec. 4.1.2) skip the descriptors: lanes
 // take every L-th nonzero and their sums are added across the warp.
 #pragma once
@@ -123,6 +124,11 @@ struct EpiSpmmPlain {
   }
 };
 
+// Depth of the SpMM's block ring.  A third stage (two CTAs per SM still fit) took the
+// shared memory per SM past the point where the driver shrinks L1: k = 8 on R-MAT scale
+// 22 went from 0.458 to 0.548 ms.
+constexpr int kSpmmStages = 2;
+
 struct SpmmGeometry {
   double* acc;      // (nb + 1) x KC FP64 boundary-row accumulators of this chunk
   int kc;           // columns in this chunk (a multiple of VW)
@@ -140,10 +146,13 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int L = 32 / T;                    // lanes walked at once (one pass)
   constexpr int U1 = 8;                        // row slices per round of a single-row tile
   constexpr int VE = 4;
-  __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ StageInfo info[2];
-  __shared__ int wt_row[2][2 * kTilesPerBlock];                   // per-warp first / last runs
-  __shared__ __align__(16) float wt_val[2][2 * kTilesPerBlock][KC];
+  constexpr int NE = 2 * kTilesPerBlock;       // table entries of a block: each warp's first / last run
+  constexpr int S = kSpmmStages;
+  __shared__ __align__(8) uint64_t mbar[S];
+  __shared__ StageInfo info[S];
+  __shared__ int arrive[S];                    // warps done with the stage's block
+  __shared__ int wt_row[S][NE];
+  __shared__ __align__(16) float wt_val[S][NE][KC];
   extern __shared__ __align__(128) unsigned char dyn_smem[];
 
   const int tid = threadIdx.x;
@@ -187,21 +196,29 @@ __global__ void __launch_bounds__(kThreads, 2)
   };
 
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&mbar[i], 1);
+      arrive[i] = 0;
+    }
     fence_mbar_init();
   }
   __syncthreads();
   if (tid == 0) {
-    int xb, xe; uint32_t yb, ye;
-    if (blockIdx.x < g.nb) { geom_of(blockIdx.x, xb, xe, yb, ye); issue(0, xb, xe, yb, ye); }
-    if (blockIdx.x + G < g.nb) { geom_of(blockIdx.x + G, xb, xe, yb, ye); issue(1, xb, xe, yb, ye); }
+    for (int i = 0; i < S; ++i) {
+      const int v = blockIdx.x + i * G;
+      if (v >= g.nb) break;
+      int xb, xe; uint32_t yb, ye;
+      geom_of(v, xb, xe, yb, ye);
+      issue(i, xb, xe, yb, ye);
+    }
   }
 
-  int it = 0;
-  for (int v = blockIdx.x; v < g.nb; v += G, ++it) {
-    const int s = it & 1;
-    const uint32_t par = (it >> 1) & 1;
+  // The warps move through the ring on their own: no block-wide barrier.  The last warp
+  // to finish a block (a shared-memory arrival count) adds up the block's cross-warp table
+  // and refills the stage with the block S steps ahead.
+  int s = 0;
+  uint32_t par = 0;
+  for (int v = blockIdx.x; v < g.nb; v += G) {
     const int ti = v * kTilesPerBlock + warp;
     const bool tile_ok = ti < g.tile_num;
     // the tile's bounds and its 32 lane descriptors (one per thread), read before the
@@ -214,15 +231,22 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int j = ti * kOmega + lane;
       if (j < g.lane_num) dreg = ld_stream(g.lane_desc + j, pol_stream);
     }
-    int nxb = 0, nxe = 0; uint32_t nyb = 0, nye = 0;
-    const bool refill = (tid == 0) && (v + 2 * G < g.nb);
-    if (refill) geom_of(v + 2 * G, nxb, nxe, nyb, nye);
-
-    const bool ok = mbar_wait_bounded(&mbar[s], par);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(&g.red->err, 1);
-      mbar_wait_bounded(&mbar[s], par);
-      if (v + G < g.nb) mbar_wait_bounded(&mbar[s ^ 1], ((it + 1) >> 1) & 1);
+    const bool ok = mbar_wait_bounded(&mbar[s], par, g.wait_limit);
+    if (!__all_sync(0xffffffffu, ok)) {
+      // this warp gives up: it records the error and waits, with the default limit, for
+      // the copies that may still be landing in the ring (this block and the next S - 1
+      // of the CTA; a wait for a copy never issued simply runs out), then returns.  A
+      // warp that gives up never arrives, so the other warps' waits run out in turn.
+      if (lane == 0) atomicOr(&g.red->err, 1);
+      int ss = s;
+      uint32_t pp = par;
+      for (int m = 0; m < S && v + m * G < g.nb; ++m) {
+        mbar_wait_bounded(&mbar[ss], pp);
+        if (++ss == S) {
+          ss = 0;
+          pp ^= 1u;
+        }
+      }
       return;
     }
     const StageInfo in = info[s];
@@ -315,14 +339,18 @@ __global__ void __launch_bounds__(kThreads, 2)
           const uint32_t rm = ~(d >> 18) & valid;  // right steps
           const int xo = (int)(d & 511u);
           const int y0 = active ? (int)((d >> 9) & 511u) : (g.n_rows - y_ws);
+          // right step k takes the lane's nonzero k - (down steps before k); the slices
+          // are only read under the predicate that loaded them
+          const uint32_t rk = c_ok ? rm : 0u;
           VT xv[kSigmaMax];
           float wv[kSigmaMax];
+          int ndk = 0;
 #pragma unroll
           for (int k = 0; k < kSigmaMax; ++k) {
             xv[k] = V::zero();
             wv[k] = 0.f;
-            if (((rm >> k) & 1u) && c_ok)
-              xv[k] = gather(xo + k - __popc(dm & ((1u << k) - 1u)), wv[k]);
+            if ((rk >> k) & 1u) xv[k] = gather(xo + k - ndk, wv[k]);
+            ndk += (int)((dm >> k) & 1u);
           }
           VT sum = V::zero(), head = V::zero();
 #pragma unroll
@@ -369,16 +397,20 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (in.endv >= in.x_be) walk(std::integral_constant<bool, true>{});
       else walk(std::integral_constant<bool, false>{});
     }
+    // arrival: this warp's reads of the stage and its table entries are done
     fence_proxy_async_smem();
-    __syncthreads();
-    if (refill) issue(s, nxb, nxe, nyb, nye);
-
-    // rows spread over several warps of the block (never a boundary row): the warp
-    // holding a row's first table entry adds up its entries
-    if (gl == 0) {
-#pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        const int e = 2 * warp + h;
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) {
+      __threadfence_block();
+      last = atomicAdd(&arrive[s], 1) == kWarps - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence_block();
+      // rows spread over several warps of the block (never a boundary row): the table's
+      // first entry of each row adds up the row's entries
+      for (int e = gl; e < NE; e += L) {
         const int r = wrow[e];
         if (r < 0 || !c_ok) continue;
         int prev = e - 1;
@@ -386,16 +418,30 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (prev >= 0 && wrow[prev] == r) continue;      // not the first entry of its row
         float tot[VW];
 #pragma unroll
-        for (int k = 0; k < VW; ++k) tot[k] = 0.f;
-        for (int q = e; q < 2 * kTilesPerBlock; ++q) {
+        for (int q = 0; q < VW; ++q) tot[q] = 0.f;
+        for (int q = e; q < NE; ++q) {
           const int rq = wrow[q];
           if (rq < 0) continue;
           if (rq != r) break;
 #pragma unroll
-          for (int k = 0; k < VW; ++k) tot[k] += wval[q][c + k];
+          for (int u = 0; u < VW; ++u) tot[u] += wval[q][c + u];
         }
         epi.row(r, c, V::from(tot));
       }
+      __syncwarp();
+      if (lane == 0) {
+        arrive[s] = 0;
+        const int vn = v + S * G;
+        if (vn < g.nb) {
+          int xb, xe; uint32_t yb, ye;
+          geom_of(vn, xb, xe, yb, ye);
+          issue(s, xb, xe, yb, ye);
+        }
+      }
+    }
+    if (++s == S) {
+      s = 0;
+      par ^= 1u;
     }
   }
 }
@@ -423,10 +469,10 @@ cudaError_t launch_spmm(const merbit_plan_s* p, const float* vals, const float* 
                         const SpmmGeometry& sg, const Epi& epi, cudaStream_t st) {
   if (p->nb == 0) return cudaSuccess;
   auto kern = merbit_spmm_kernel<KC, VW, Epi>;
-  const size_t smem = 2 * stage_bytes<float>(p->sigma, kTilesPerBlock);
-  const size_t smem_max = 2 * stage_bytes<float>(kSigmaMax, kTilesPerBlock);
-  int grid = persistent_grid(reinterpret_cast<const void*>(kern), kThreads, smem, smem_max,
-                             p->num_sms);
+  const void* kp = reinterpret_cast<const void*>(kern);
+  const size_t smem = kSpmmStages * stage_bytes<float>(p->sigma, kTilesPerBlock);
+  const size_t smem_max = kSpmmStages * stage_bytes<float>(kSigmaMax, kTilesPerBlock);
+  int grid = persistent_grid(kp, kThreads, smem, smem_max, p->num_sms);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   if ((int64_t)grid > p->nb) grid = (int)p->nb;
   kern<<<grid, kThreads, smem, st>>>(p->geom(), sg, vals, X, ldx, epi);
