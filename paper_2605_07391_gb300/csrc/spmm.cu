@@ -1,13 +1,17 @@
 // Host side of the batched product Y = scale * A X (row-major X and Y, f32): column
-// chunks of 32, 16 or 8 through merbit_spmm_kernel, with 16-byte row slices when every
-// slice is 16-byte aligned and scalar slices otherwise.
+// chunks of 32, 16 or 8 through merbit_spmm_kernel.  A thread's row slice is 4 columns
+// (16 bytes) when every slice is 16-byte aligned, 8 columns in chunks of 16 and 32 when k
+// is also a multiple of 8, and one column otherwise.  R-MAT scale 22: 8-column slices
+// took k = 16 from 0.707 to 0.664 ms and k = 32 from 1.222 to 1.011 ms, but k = 8 (one
+// lane per thread, a whole tile per pass) from 0.456 to 0.570 ms.
 #include "spmm_kernel.cuh"
 
 namespace merbit {
 
 namespace {
 
-template <int VW>
+// VW: slice width of 8-column chunks, VWW: of 16- and 32-column chunks
+template <int VW, int VWW>
 cudaError_t spmm_chunks(const merbit_plan_s* p, const float* vals, const float* X, int64_t k,
                         int64_t ldx, float* Y, int64_t ldy, float scale, bool gated, double* acc,
                         cudaStream_t st) {
@@ -17,8 +21,8 @@ cudaError_t spmm_chunks(const merbit_plan_s* p, const float* vals, const float* 
     SpmmGeometry sg{acc, (int)std::min<int64_t>(left, kc)};
     EpiSpmmPlain epi{Y + c0, (int)ldy, scale, gated};
     cudaError_t e;
-    if (kc == 32) e = launch_spmm<32, VW>(p, vals, X + c0, (int)ldx, sg, epi, st);
-    else if (kc == 16) e = launch_spmm<16, VW>(p, vals, X + c0, (int)ldx, sg, epi, st);
+    if (kc == 32) e = launch_spmm<32, VWW>(p, vals, X + c0, (int)ldx, sg, epi, st);
+    else if (kc == 16) e = launch_spmm<16, VWW>(p, vals, X + c0, (int)ldx, sg, epi, st);
     else e = launch_spmm<8, VW>(p, vals, X + c0, (int)ldx, sg, epi, st);
     if (e != cudaSuccess) return e;
     c0 += sg.kc;
@@ -32,8 +36,9 @@ cudaError_t spmm_dispatch(const merbit_plan_s* p, const float* vals, const float
   const bool vec = k % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 &&
                    (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
-  return vec ? spmm_chunks<4>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st)
-             : spmm_chunks<1>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st);
+  if (!vec) return spmm_chunks<1, 1>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st);
+  return k % 8 == 0 ? spmm_chunks<4, 8>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st)
+                    : spmm_chunks<4, 4>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st);
 }
 
 }  // namespace

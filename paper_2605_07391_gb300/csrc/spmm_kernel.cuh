@@ -100,6 +100,40 @@ template <> struct SpmmVec<4> {
   }
 };
 
+// Two 16-byte halves: a thread's slice is a whole 32-byte row of an 8-column chunk.
+struct Float8 {
+  float4 a, b;
+};
+template <> struct SpmmVec<8> {
+  using T = Float8;
+  using H = SpmmVec<4>;
+  static __device__ __forceinline__ T zero() { return T{H::zero(), H::zero()}; }
+  static __device__ __forceinline__ T load(const float* p) { return T{H::load(p), H::load(p + 4)}; }
+  static __device__ __forceinline__ void fma(float w, const T& x, T& s) {
+    H::fma(w, x.a, s.a);
+    H::fma(w, x.b, s.b);
+  }
+  static __device__ __forceinline__ float get(const T& v, int i) {
+    return i < 4 ? H::get(v.a, i) : H::get(v.b, i - 4);
+  }
+  static __device__ __forceinline__ T from(const float (&a)[8]) {
+    return T{make_float4(a[0], a[1], a[2], a[3]), make_float4(a[4], a[5], a[6], a[7])};
+  }
+  static __device__ __forceinline__ void add(T& s, const T& x) {
+    H::add(s.a, x.a);
+    H::add(s.b, x.b);
+  }
+  static __device__ __forceinline__ T shfl_up(const T& v, int d) {
+    return T{H::shfl_up(v.a, d), H::shfl_up(v.b, d)};
+  }
+  static __device__ __forceinline__ T shfl_xor(const T& v, int d) {
+    return T{H::shfl_xor(v.a, d), H::shfl_xor(v.b, d)};
+  }
+  static __device__ __forceinline__ T shfl(const T& v, int src) {
+    return T{H::shfl(v.a, src), H::shfl(v.b, src)};
+  }
+};
+
 // Epilogue of the SpMM: Y[r, c..c+VW) = scale * (A X)[r, c..c+VW).  row() takes f32 row sums
 // (called by the thread owning columns c..c+VW), row64 one column of a block-shared row
 // summed in FP64 (finalize kernel).  A gated launch does nothing once an iterative driver
@@ -118,6 +152,10 @@ struct EpiSpmmPlain {
   __device__ __forceinline__ void row(int r, int c, const float4& s) const {
     *reinterpret_cast<float4*>(y + (size_t)r * ldy + c) =
         make_float4(scale * s.x, scale * s.y, scale * s.z, scale * s.w);
+  }
+  __device__ __forceinline__ void row(int r, int c, const Float8& s) const {
+    row(r, c, s.a);
+    row(r, c + 4, s.b);
   }
   __device__ __forceinline__ void row64(int r, int c, double s) const {
     y[(size_t)r * ldy + c] = static_cast<float>(static_cast<double>(scale) * s);
@@ -145,6 +183,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int T = KC / VW;                   // threads per lane, one slice of VW columns each
   constexpr int L = 32 / T;                    // lanes walked at once (one pass)
   constexpr int U1 = 8;                        // row slices per round of a single-row tile
+  constexpr int HB = VW == 8 ? kSigmaMax / 2 : kSigmaMax;   // steps per batch of gathers
+  static_assert(kSigmaMax % HB == 0, "step batches");
   constexpr int VE = 4;
   constexpr int NE = 2 * kTilesPerBlock;       // table entries of a block: each warp's first / last run
   constexpr int S = kSpmmStages;
@@ -339,28 +379,35 @@ __global__ void __launch_bounds__(kThreads, 2)
           const uint32_t rm = ~(d >> 18) & valid;  // right steps
           const int xo = (int)(d & 511u);
           const int y0 = active ? (int)((d >> 9) & 511u) : (g.n_rows - y_ws);
-          // right step k takes the lane's nonzero k - (down steps before k); the slices
-          // are only read under the predicate that loaded them
+          // right step k takes the lane's nonzero k - (down steps before k); a batch of
+          // HB steps has all its slices in flight before any is used (HB = sigma_max, or
+          // half of it for 32-byte slices, which would not fit the registers)
           const uint32_t rk = c_ok ? rm : 0u;
-          VT xv[kSigmaMax];
-          float wv[kSigmaMax];
+          VT sum = V::zero(), head = V::zero();
           int ndk = 0;
 #pragma unroll
-          for (int k = 0; k < kSigmaMax; ++k) {
-            xv[k] = V::zero();
-            wv[k] = 0.f;
-            if ((rk >> k) & 1u) xv[k] = gather(xo + k - ndk, wv[k]);
-            ndk += (int)((dm >> k) & 1u);
-          }
-          VT sum = V::zero(), head = V::zero();
+          for (int k0 = 0; k0 < kSigmaMax; k0 += HB) {
+            VT xv[HB];
+            float wv[HB];
+            int nd_b = ndk;
 #pragma unroll
-          for (int k = 0; k < kSigmaMax; ++k) {
-            V::fma(wv[k], xv[k], sum);           // zero at down steps and past the lane
-            if ((dm >> k) & 1u) {
-              const int nd = __popc(dm & ((1u << k) - 1u));
-              if (nd == 0) head = sum;
-              else if (c_ok) epi.row(y_ws + y0 + nd, c, sum);
-              sum = V::zero();
+            for (int u = 0; u < HB; ++u) {
+              const int k = k0 + u;
+              xv[u] = V::zero();
+              wv[u] = 0.f;
+              if ((rk >> k) & 1u) xv[u] = gather(xo + k - nd_b, wv[u]);
+              nd_b += (int)((dm >> k) & 1u);
+            }
+#pragma unroll
+            for (int u = 0; u < HB; ++u) {
+              const int k = k0 + u;
+              V::fma(wv[u], xv[u], sum);         // zero at down steps and past the lane
+              if ((dm >> k) & 1u) {
+                if (ndk == 0) head = sum;
+                else if (c_ok) epi.row(y_ws + y0 + ndk, c, sum);
+                sum = V::zero();
+                ++ndk;
+              }
             }
           }
           // runs across the pass's lanes: OC_l = run open after lane l obeys
