@@ -1,9 +1,10 @@
 // Host side of the batched product Y = scale * A X (row-major X and Y, f32): column
 // chunks of 32, 16 or 8 through merbit_spmm_kernel.  A thread's row slice is 4 columns
-// (16 bytes) when every slice is 16-byte aligned, 8 columns in chunks of 16 and 32 when k
-// is also a multiple of 8, and one column otherwise.  R-MAT scale 22: 8-column slices
-// took k = 16 from 0.707 to 0.664 ms and k = 32 from 1.222 to 1.011 ms, but k = 8 (one
-// lane per thread, a whole tile per pass) from 0.456 to 0.570 ms.
+// (16 bytes) when every slice is 16-byte aligned, 8 columns (one 32-byte load) in chunks
+// of 16 and 32 when k and ldx are multiples of 8 and X is 32-byte aligned, and one column
+// otherwise.  R-MAT scale 22: 8-column slices took k = 16 from 0.707 to 0.599 ms and
+// k = 32 from 1.222 to 1.003 ms, but k = 8 (one lane per thread, a whole tile per pass)
+// from 0.456 to 0.490 ms, so 8-column chunks keep 4-column slices.
 #include "spmm_kernel.cuh"
 
 namespace merbit {
@@ -37,7 +38,9 @@ cudaError_t spmm_dispatch(const merbit_plan_s* p, const float* vals, const float
                    (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
   if (!vec) return spmm_chunks<1, 1>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st);
-  return k % 8 == 0 ? spmm_chunks<4, 8>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st)
+  // 8-column slices are read by one 32-byte load, which needs 32-byte alignment
+  const bool v8 = k % 8 == 0 && ldx % 8 == 0 && (reinterpret_cast<uintptr_t>(X) & 31) == 0;
+  return v8 ? spmm_chunks<4, 8>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st)
                     : spmm_chunks<4, 4>(p, vals, X, k, ldx, Y, ldy, scale, gated, acc, st);
 }
 

@@ -100,7 +100,8 @@ template <> struct SpmmVec<4> {
   }
 };
 
-// Two 16-byte halves: a thread's slice is a whole 32-byte row of an 8-column chunk.
+// Two 16-byte halves: a thread's slice is a whole 32-byte row of an 8-column chunk,
+// read by one 32-byte load (its address must be 32-byte aligned).
 struct Float8 {
   float4 a, b;
 };
@@ -108,7 +109,14 @@ template <> struct SpmmVec<8> {
   using T = Float8;
   using H = SpmmVec<4>;
   static __device__ __forceinline__ T zero() { return T{H::zero(), H::zero()}; }
-  static __device__ __forceinline__ T load(const float* p) { return T{H::load(p), H::load(p + 4)}; }
+  static __device__ __forceinline__ T load(const float* p) {
+    T v;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v.a.x), "=f"(v.a.y), "=f"(v.a.z), "=f"(v.a.w), "=f"(v.b.x), "=f"(v.b.y), "=f"(v.b.z),
+          "=f"(v.b.w)
+        : "l"(p));
+    return v;
+  }
   static __device__ __forceinline__ void fma(float w, const T& x, T& s) {
     H::fma(w, x.a, s.a);
     H::fma(w, x.b, s.b);

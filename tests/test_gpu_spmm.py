@@ -87,3 +87,20 @@ def test_spmm_full_rmat22(cuda_device, k):
 def test_spmm_wide(cuda_device):
     """k = 300: nine 32-column chunks and a 12-column remainder in a 16-column chunk."""
     _run(inputs.rmat_transition(11, 16, 5), 300)
+
+
+@pytest.mark.parametrize("k,ldx,shift", [(16, 16, 0), (16, 16, 4), (32, 36, 0), (24, 24, 0), (48, 56, 8)])
+def test_spmm_slice_widths(cuda_device, k, ldx, shift):
+    # 32-byte slices need k and ldx multiples of 8 and X 32-byte aligned; a 16-byte shift
+    # of X, or ldx = 36, takes the 16-byte slices, and k = 24 mixes both (chunks 16 + 8)
+    a = inputs.add_hubs(inputs.rmat_uniform(13, 16, 3, 3), 2, 3000, 6000, 5)
+    p, _ = make_plan(a)
+    vals = torch.from_numpy(a.val).to("cuda", torch.float32)
+    rng = np.random.default_rng(k + ldx + shift)
+    buf = torch.from_numpy(rng.random(a.n_cols * ldx + 64)).to("cuda", torch.float32)
+    X = buf[shift:shift + a.n_cols * ldx].view(a.n_cols, ldx)[:, :k]
+    Y = torch.full((a.n_rows, k), float("nan"), device="cuda")
+    mb.spmm(p, vals, X, Y)
+    p.sync()
+    Yr, D = oracle.spmm(a.row_ptr, a.col, as_f64(vals), as_f64(X))
+    check_rel(as_f64(Y).ravel(), Yr.ravel(), D.ravel(), 1e-5, f"k={k} ldx={ldx} shift={shift}")
