@@ -1,5 +1,5 @@
 // Host side of the batched product Y = scale * A X (row-major X and Y, f32): column
-// chunks of 32, 16 or 8 through merbit_spmm_kernel.  A thread's row slice is 4 columns
+// chunks of 32, 16, 8 or 4 through merbit_spmm_kernel.  A thread's row slice is 4 columns
 // (16 bytes) when every slice is 16-byte aligned, 8 columns (one 32-byte load) in chunks
 // of 16 and 32 when k and ldx are multiples of 8 and X is 32-byte aligned, and one column
 // otherwise.  R-MAT scale 22: 8-column slices took k = 16 from 0.707 to 0.599 ms and
@@ -18,13 +18,14 @@ cudaError_t spmm_chunks(const merbit_plan_s* p, const float* vals, const float* 
                         cudaStream_t st) {
   for (int64_t c0 = 0; c0 < k;) {
     const int64_t left = k - c0;
-    const int kc = left >= 32 ? 32 : left > 8 ? 16 : 8;
+    const int kc = left >= 32 ? 32 : left > 8 ? 16 : left > 4 ? 8 : 4;
     SpmmGeometry sg{acc, (int)std::min<int64_t>(left, kc)};
     EpiSpmmPlain epi{Y + c0, (int)ldy, scale, gated};
     cudaError_t e;
     if (kc == 32) e = launch_spmm<32, VWW>(p, vals, X + c0, (int)ldx, sg, epi, st);
     else if (kc == 16) e = launch_spmm<16, VWW>(p, vals, X + c0, (int)ldx, sg, epi, st);
-    else e = launch_spmm<8, VW>(p, vals, X + c0, (int)ldx, sg, epi, st);
+    else if (kc == 8) e = launch_spmm<8, VW>(p, vals, X + c0, (int)ldx, sg, epi, st);
+    else e = launch_spmm<4, VW>(p, vals, X + c0, (int)ldx, sg, epi, st);
     if (e != cudaSuccess) return e;
     c0 += sg.kc;
   }

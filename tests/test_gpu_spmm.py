@@ -28,7 +28,7 @@ def _run(a, k, ldx=None, seed=3, calls=1):
     return Y
 
 
-@pytest.mark.parametrize("k", [1, 3, 8, 13, 16, 32, 40])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 8, 12, 13, 16, 32, 36, 40])
 def test_spmm_rmat14(cuda_device, k):
     _run(inputs.rmat_transition(14, 16, 1), k)
 
