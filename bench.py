@@ -500,7 +500,7 @@ def run_many_graphs(args, dev, stream) -> dict:
     # sigma x block kernel by measurement (batches keep 8 tiles per block and 32-bit
     # descriptors; the block size is listed for completeness)
     tune, times = mb.autotune(rp, col, vals, sigmas=(14, 12, 10, 7), blocks=(8,),
-                              kernels=("classic", "split"), hots=(0,), reps=3, stream=stream)
+                              kernels=("classic", "split", "split2"), hots=(0,), reps=3, stream=stream)
     best = tune["sigma"]
     res["autotune"] = {"best": tune, "ms_per_spmv": {f"s{k[0]}_W{k[1]}_{k[2]}": v for k, v in times.items()}}
     torch.cuda.synchronize(dev)

@@ -30,8 +30,9 @@ bool split_config_f64(const merbit_plan_s* p, Geometry& g, int& grid, size_t& sm
   // the launch the product itself makes (the automatic choice may take a two-stage ring);
   // when the product would fall back to the classic kernel, the split kernel's own launch
   const Geometry g0 = g;
-  if (split_config<double, double, double, EpiPlain<double, double>>(p, g, grid, smem, p->spmv_kernel != MERBIT_KERNEL_SPLIT &&
-                                                              p->spmv_kernel != MERBIT_KERNEL_SPLIT2))
+  const int kind = p->spmv_kernel;
+  if (kind != MERBIT_KERNEL_CLASSIC &&
+      split_config<double, double, double, EpiPlain<double, double>>(p, g, grid, smem, kind != MERBIT_KERNEL_AUTO))
     return true;
   g = g0;
   return split_config<double, double, double, EpiPlain<double, double>>(p, g, grid, smem, true);

@@ -1080,6 +1080,14 @@ constexpr int64_t kFoldMaxBlocks = 1024;
 // table is only added while the SM's shared memory stays at or below that carveout.
 constexpr size_t kSharedPerSmKeepL1 = 196 * 1024;
 
+// The automatic choice takes the three-stage ring only while two CTAs' rings stay within
+// this much shared memory per SM; above it the L1 left for the x gather costs more than
+// the deeper ring gains.  R-MAT-24, three vs two stages: f32 sigma 12 (149 KB per SM)
+// 1.185 vs 1.194 ms, sigma 13 (161 KB) 1.164 vs 1.167, sigma 14 (174 KB) 1.175 vs 1.151;
+// f64 sigma 9 (168 KB) 2.074 vs 2.093, sigma 10 (187 KB) 1.957 vs 1.951, sigma 12 (224 KB)
+// 2.827 vs 1.898.
+constexpr size_t kDeepRingSharedPerSm = 168 * 1024;
+
 template <typename XT>
 inline size_t add_hot_table(const merbit_plan_s* p, Geometry& g, const void* kern, size_t stages,
                             int per_sm) {
@@ -1102,6 +1110,9 @@ bool split_config(const merbit_plan_s* p, Geometry& g, int& grid, size_t& smem, 
   auto kern = merbit_spmv_split_kernel<VT, XT, AT, Epi>;
   const void* kp = reinterpret_cast<const void*>(kern);
   g.stages = p->spmv_kernel == MERBIT_KERNEL_SPLIT2 ? 2 : kSplitStages;
+  if (!forced && g.stages == kSplitStages &&
+      2 * kSplitStages * stage_bytes<VT>(p->sigma, p->tiles_per_block) > kDeepRingSharedPerSm)
+    g.stages = 2;
   size_t stages = (size_t)g.stages * stage_bytes<VT>(p->sigma, p->tiles_per_block);
   grid = persistent_grid(kp, kSplitThreads, stages, stages, p->num_sms);
   if (!forced && grid < 2 * p->num_sms && g.stages == kSplitStages) {
