@@ -135,9 +135,9 @@ merbit_status merbit_plan_export(merbit_plan_t plan, uint32_t* tile_x, uint32_t*
  *     the producers' work on block i + 1).
  *   A split kernel that cannot hold one CTA's stages on an SM (large sigma x block
  *   size with 8-byte values) gives way to CLASSIC.
- *   MERBIT_KERNEL_AUTO (the default): SPLIT for 32- and 64-bit values while two of
- *     its CTAs fit on an SM (its three stages at the plan's sigma), else SPLIT2 while
- *     two of those fit, else CLASSIC; CLASSIC for 16-bit values. */
+ *   MERBIT_KERNEL_AUTO (the default): SPLIT while two of its CTAs fit on an SM and
+ *     their three stages at the plan's sigma take at most 168 KB of shared memory per
+ *     SM, else SPLIT2 while two of those fit, else CLASSIC. */
 enum {
   MERBIT_KERNEL_AUTO = 0,
   MERBIT_KERNEL_CLASSIC = 1,

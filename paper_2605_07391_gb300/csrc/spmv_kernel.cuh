@@ -1136,9 +1136,9 @@ template <typename VT, typename XT, typename AT, typename Epi>
 cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, const Epi& epi,
                         cudaStream_t st) {
   if (p->nb == 0) return cudaSuccess;
-  // The split kernel is the default for 32- and 64-bit values while two of its CTAs fit
-  // on an SM (measured on sm_103a, R-MAT scale 21 and 24: 15-30 % faster than the classic
-  // kernel there, slower with one CTA per SM, level for 16-bit values).
+  // The split kernel is the default while two of its CTAs fit on an SM (measured on
+  // sm_103a, R-MAT scale 21 and 24: 15-30 % faster than the classic kernel for 32- and
+  // 64-bit values, 11 % for 16-bit values at sigma 14, slower with one CTA per SM).
   Geometry g = p->geom();
   // few blocks: the block kernel finishes the product itself (no second launch)
   g.fold = p->nb <= kFoldMaxBlocks;
@@ -1148,8 +1148,7 @@ cudaError_t launch_spmv(const merbit_plan_s* p, const VT* vals, const XT* x, con
   // A split kernel that was asked for but cannot hold even one CTA's stages on an SM (large
   // sigma x block size with 8-byte values) gives way to the classic kernel, whose ring
   // has two stages.
-  if (kind == MERBIT_KERNEL_SPLIT || kind == MERBIT_KERNEL_SPLIT2 ||
-      (kind == MERBIT_KERNEL_AUTO && sizeof(VT) >= 4)) {
+  if (kind == MERBIT_KERNEL_SPLIT || kind == MERBIT_KERNEL_SPLIT2 || kind == MERBIT_KERNEL_AUTO) {
     size_t smem = 0;
     split = split_config<VT, XT, AT, Epi>(p, g, grid, smem, kind != MERBIT_KERNEL_AUTO);
     if (split) merbit_spmv_split_kernel<VT, XT, AT, Epi><<<grid, kSplitThreads, smem, st>>>(g, vals, x, epi);
