@@ -222,15 +222,20 @@ merbit_status merbit_spmv_ex(merbit_plan_t plan, merbit_dtype vals_dtype, merbit
  * merbit_spmm — Y = A X for k right-hand sides at once (the batching extension
  * of the method: k personalisation vectors in one pass over the plan).  X is
  * row-major n_cols x k with leading dimension ldx >= k, Y row-major n_rows x k
- * with ldy >= k, all f32 device pointers; vals f32, 16-byte aligned.  Columns
- * are processed in chunks of up to 32; each nonzero's column index and value are
- * read once per chunk and the gathered row slice X[col, chunk] serves the whole
- * chunk.  When k, ldx and ldy are multiples of 4 and X, Y are 16-byte aligned the
- * slices are read as 16-byte vectors, otherwise element by element.  Y's first
- * k columns are fully overwritten (rows of A with no nonzeros get 0).
+ * with ldy >= k, all f32 device pointers; vals f32, 16-byte aligned.  The plan
+ * must have 8 tiles per block and sigma <= 14.  Columns are processed in chunks of
+ * 32, 16, 8 or 4; each nonzero's column index and value are read once per chunk and
+ * the gathered row slice X[col, chunk] serves the whole chunk.  When k, ldx and ldy
+ * are multiples of 4 and X, Y are 16-byte aligned the slices are read as 16-byte
+ * vectors (32-byte ones in chunks of 16 and 32 when k and ldx are also multiples of 8
+ * and X is 32-byte aligned), otherwise element by element.  Y's first k columns are
+ * fully overwritten (rows of A with no nonzeros get 0).
  * Asynchronous on `stream`; allocates (once per plan) a (block_num + 1) x 32
- * FP64 accumulator for rows shared between blocks.  Errors: EINVAL (NULL
- * pointers, k < 0, ldx < k, ldy < k, misaligned vals), ENOMEM, ECUDA.
+ * FP64 accumulator for rows shared between blocks.  A stage wait that gives up
+ * (bounded; see merbit_plan_set_wait_limit) is reported by merbit_plan_sync as
+ * MERBIT_EDEVICE.  Errors: EINVAL (NULL pointers, k < 0, ldx < k, ldy < k,
+ * misaligned vals, a plan of other than 8 tiles per block or sigma > 14), ENOMEM,
+ * ECUDA.
  */
 merbit_status merbit_spmm(merbit_plan_t plan, const float* vals, const float* X, float* Y,
                           int64_t k, int64_t ldx, int64_t ldy, void* stream);
