@@ -11,8 +11,9 @@
 //   * two block kernels share the stages and the per-tile reduction:
 //     merbit_spmv_kernel (all threads gather, then all reduce; two stages) and
 //     merbit_spmv_split_kernel (producer threads gather for the next blocks
-//     while consumer threads reduce the current one; three stages), which keeps
-//     the SM's gather path busy and is the default where two CTAs fit per SM;
+//     while consumer threads reduce the current one; a ring of three or two
+//     stages), which keeps the SM's gather path busy and is the default where two
+//     CTAs fit per SM;
 //   * matrix streams use an L2 evict_first policy, the x gather an
 //     evict_last policy (x is reused by every block and, in PageRank, by the
 //     next launch);
