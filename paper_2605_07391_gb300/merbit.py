@@ -221,7 +221,8 @@ class Plan:
         return t
 
     def set_kernel(self, kernel: str):
-        """Block kernel for later products: "auto", "classic" or "split"."""
+        """Block kernel for later products (merbit_plan_set_kernel): "auto", "classic",
+        "split" (three-stage ring) or "split2" (two-stage ring)."""
         _check("merbit_plan_set_kernel", load().merbit_plan_set_kernel(self.handle, KERNELS[kernel]))
 
     def set_wait_limit(self, polls: int):
